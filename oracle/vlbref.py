@@ -1,0 +1,855 @@
+"""FP64 oracle: the volumetric LB method written out phase by phase.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): only tests, the smoke
+check and the benchmark's CPU-baseline leg use this module.
+
+Conventions
+-----------
+* Lattice units, delta_x = delta_t = c = 1.
+* Cell (i, j) covers [i, i+1] x [j, j+1]; its node sits at the cell centre
+  (i + 1/2, j + 1/2) -- the volumetric interpretation of Sec. 2 / Fig. 1.
+* Fields are numpy arrays indexed [y, x]; populations have shape (9, ny, nx).
+* Walls sit on the cell faces of the domain boundary.
+
+Readings of passages the paper leaves open (each one is also listed in the
+design notes of the repository):
+
+R1  Solid fraction (Sec. 2, "directly determined by the position"): the exact
+    area of disk ∩ cell.  A cell is *solid* for a particle when its four
+    corners lie in the closed disk, *fluid* when its nearest point lies at
+    distance >= R, else *interface*.  Those two tests run on positions
+    rounded to a 2^-20 fixed-point grid, in integers, so that both
+    implementations take the same integer decisions.  Several particles may
+    own one cell (at most 4); their fractions add, and are scaled down so
+    that they sum to 1 if they exceed it (only under contact overlap).
+R2  Walls (Sec. 3): halfway bounce-back for f; bounce-back for g at adiabatic
+    walls; anti-bounce-back g_i = -gbar_opp(i) + 2 g_i^eq(T_w) at walls held
+    at T_w.  A population that crosses a domain corner is handled by the
+    wall normal to y.
+R3  Time levels (Sec. 2.3, Eq. 8 and the forward-Euler remark at the end of
+    Sec. 2.3): the particle state used by the correction of step n -> n+1 is
+    advanced explicitly from the force of level n (lagged coupling).
+R4  Buoyancy on the fluid (Sec. 3.3) is weighted by (1 - f_s) so that u = u_s
+    stays exact in solid cells (Sec. 2.1); the circular dependence between
+    T (Eq. 25) and u (Eq. 9) through the buoyancy force is closed by solving
+    both at t + dt jointly (closed form below).
+R5  Contact (Sec. 2.3 cites Glowinski et al. 2001 without its formula): the
+    normalised short-range repulsion
+      F_ij = (c_ij / eps_p) * (max(0, R_i + R_j + zeta - d_ij) / zeta)^2
+             * (X_i - X_j) / d_ij,
+    c_ij = |rho_r - 1| rho_f |g| pi max(R_i, R_j)^2, and its image-particle
+    form at walls with eps_w.  It is central (no torque).
+R6  Initial state: f* = f^eq(1, 0) corrected with f_s^0 (Eq. 8); the internal
+    energy is mixed by volume, eps^0 = (1 - f_s) c_vf T_f + sum_p f_s,p c_vs
+    T_p, T^0 = eps^0 / c_v; g^0 = g^eq(eps^0, T^0); q_c^0 = 0 and
+    [df_s/dt]^0 = 0.
+R7  Domain: fractions exist only for cells inside the domain; a particle may
+    not cross a periodic boundary.
+"""
+from __future__ import annotations
+
+import dataclasses
+import functools
+import math
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# D2Q9 velocity set (Eq. 2) and the orthogonal moment matrix (Eq. 4).
+# --------------------------------------------------------------------------
+
+
+def lattice_velocities() -> np.ndarray:
+    """The nine discrete velocities of Eq. 2 with c = 1, as integers."""
+    e = np.zeros((9, 2))
+    for i in range(1, 5):
+        a = (i - 1) * math.pi / 2.0
+        e[i] = (math.cos(a), math.sin(a))
+    for i in range(5, 9):
+        a = (2 * i - 1) * math.pi / 4.0
+        e[i] = (math.sqrt(2.0) * math.cos(a), math.sqrt(2.0) * math.sin(a))
+    return np.rint(e).astype(np.int64)
+
+
+E = lattice_velocities()
+EX = E[:, 0].astype(np.float64)
+EY = E[:, 1].astype(np.float64)
+OPP = np.array([int(np.where((E == -E[i]).all(axis=1))[0][0]) for i in range(9)])
+
+# Eq. 4, row by row.
+M = np.array(
+    [
+        [1, 1, 1, 1, 1, 1, 1, 1, 1],
+        [-4, -1, -1, -1, -1, 2, 2, 2, 2],
+        [4, -2, -2, -2, -2, 1, 1, 1, 1],
+        [0, 1, 0, -1, 0, 1, -1, -1, 1],
+        [0, -2, 0, 2, 0, 1, -1, -1, 1],
+        [0, 0, 1, 0, -1, 1, 1, -1, -1],
+        [0, 0, -2, 0, 2, 1, 1, -1, -1],
+        [0, 1, -1, 1, -1, 0, 0, 0, 0],
+        [0, 0, 0, 0, 0, 1, -1, 1, -1],
+    ],
+    dtype=np.float64,
+)
+MINV = np.linalg.inv(M)
+
+# Free parameters of the thermal LBE fixed in Sec. 2.2.
+ALPHA1 = -2.0
+ALPHA2 = 1.0
+BETA1 = -4.0
+BETA2 = 4.0
+
+QBITS = 20  # fixed-point grid of the integer cell tests (reading R1)
+MAX_OWNERS = 4
+
+
+def to_moments(f: np.ndarray) -> np.ndarray:
+    """m = M f for every cell (f has shape (9, ...))."""
+    return np.tensordot(M, f, axes=(1, 0))
+
+
+def from_moments(m: np.ndarray) -> np.ndarray:
+    """f = M^-1 m for every cell."""
+    return np.tensordot(MINV, m, axes=(1, 0))
+
+
+# --------------------------------------------------------------------------
+# Flow LBE (Sec. 2.1): Eqs. 3, 5, 6, 7, 8, 9.
+# --------------------------------------------------------------------------
+
+
+def flow_eq_moments(rho, ux, uy):
+    """Equilibrium moments m^eq(rho, u) of Eq. 6."""
+    u2 = ux * ux + uy * uy
+    return np.stack(
+        [
+            rho,
+            -2.0 * rho + 3.0 * rho * u2,
+            rho - 3.0 * rho * u2,
+            rho * ux,
+            -rho * ux,
+            rho * uy,
+            -rho * uy,
+            rho * (ux * ux - uy * uy),
+            rho * ux * uy,
+        ]
+    )
+
+
+def force_moments(Fx, Fy, ux, uy):
+    """Discrete force term F_m of Eq. 7."""
+    Fu = Fx * ux + Fy * uy
+    z = np.zeros_like(Fu)
+    return np.stack(
+        [
+            z,
+            6.0 * Fu,
+            -6.0 * Fu,
+            Fx + z,
+            -Fx + z,
+            Fy + z,
+            -Fy + z,
+            2.0 * (Fx * ux - Fy * uy),
+            Fx * uy + Fy * ux,
+        ]
+    )
+
+
+def feq(rho, ux, uy):
+    """f^eq(rho, u) = M^-1 m^eq(rho, u) (definition below Eq. 5)."""
+    return from_moments(flow_eq_moments(rho, ux, uy))
+
+
+def flow_rates(tau_f: float, lambda_q: float = 1.0 / 12.0, s_e: float = 1.25,
+               s0: float = 1.0, s_j: float = 1.0):
+    """Diagonal of S (Eq. 5) with the rules of Sec. 3: s0 = s_j = 1,
+    s_e = s_eps, s_p = 1/tau_f and (1/s_p - 1/2)(1/s_q - 1/2) = lambda_q."""
+    s_p = 1.0 / tau_f
+    s_q = 1.0 / (0.5 + lambda_q / (tau_f - 0.5))
+    return np.array([s0, s_e, s_e, s_j, s_q, s_j, s_q, s_p, s_p])
+
+
+def collide_flow(f, rho, ux, uy, Fx, Fy, S):
+    """Post-collision fbar from Eq. 3a: mbar = m - S (m - m^eq) + (I - S/2) F_m."""
+    m = to_moments(f)
+    meq = flow_eq_moments(rho, ux, uy)
+    Fm = force_moments(Fx, Fy, ux, uy)
+    s = np.asarray(S, dtype=np.float64).reshape((9,) + (1,) * (f.ndim - 1))
+    mbar = m - s * (m - meq) + (1.0 - 0.5 * s) * Fm
+    return from_moments(mbar)
+
+
+def flow_macroscopics(f, Fx, Fy):
+    """rho and u of Eq. 9: rho = sum f, rho u = sum e f + F/2."""
+    rho = f.sum(axis=0)
+    jx = np.tensordot(EX, f, axes=(0, 0))
+    jy = np.tensordot(EY, f, axes=(0, 0))
+    return rho, (jx + 0.5 * Fx) / rho, (jy + 0.5 * Fy) / rho
+
+
+# --------------------------------------------------------------------------
+# Streaming with walls (Eqs. 3b, 17b; reading R2).
+# --------------------------------------------------------------------------
+
+
+@functools.lru_cache(maxsize=64)
+def _source_index(nx, ny, i, periodic):
+    """Source cell x - e_i of every cell for the pull form of streaming,
+    wrapped on periodic axes; flags where it falls outside the domain."""
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    sx = xx - E[i, 0]
+    sy = yy - E[i, 1]
+    if periodic[0]:
+        sx = sx % nx
+    if periodic[1]:
+        sy = sy % ny
+    out_x = (sx < 0) | (sx >= nx)
+    out_y = (sy < 0) | (sy >= ny)
+    return yy, xx, np.clip(sy, 0, ny - 1), np.clip(sx, 0, nx - 1), out_x, out_y, sy < 0, sx < 0
+
+
+def stream_flow(fbar, periodic=(False, False)):
+    """Linear streaming f*_i(x + e_i) = fbar_i(x) (Eq. 3b), written as a
+    pull.  Where x - e_i lies outside the domain the population bounces back
+    halfway at the wall face: f*_i(x) = fbar_opp(i)(x)."""
+    _, ny, nx = fbar.shape
+    out = np.empty_like(fbar)
+    for i in range(9):
+        yy, xx, sy, sx, ox, oy, _, _ = _source_index(nx, ny, i, tuple(periodic))
+        outside = ox | oy
+        pulled = fbar[i, sy, sx]
+        out[i] = np.where(outside, fbar[OPP[i], yy, xx], pulled)
+    return out
+
+
+def stream_thermal(gbar, cref, thermal_wall, wall_T, periodic=(False, False)):
+    """Streaming of g (Eq. 17b) as a pull.  At a wall (order x-, x+, y-, y+):
+    adiabatic -> g_i(x) = gbar_opp(i)(x); held at T_w ->
+    g_i(x) = -gbar_opp(i)(x) + 2 g_i^eq(T_w).  The moving components of
+    g^eq (Eq. 19) do not depend on epsilon, so g_i^eq(T_w) is taken from
+    M^-1 n^eq(0, T_w)."""
+    _, ny, nx = gbar.shape
+    out = np.empty_like(gbar)
+    geq_wall = [from_moments(thermal_eq_moments(np.zeros(1), np.full(1, float(wall_T[w])), cref))[:, 0]
+                for w in range(4)]
+    for i in range(9):
+        yy, xx, sy, sx, ox, oy, ylow, xlow = _source_index(nx, ny, i, tuple(periodic))
+        pulled = gbar[i, sy, sx]
+        bounce = gbar[OPP[i], yy, xx]
+        # which wall: y walls first (reading R2 for corners)
+        wall = np.where(oy, np.where(ylow, 2, 3), np.where(xlow, 0, 1))
+        res = np.where(ox | oy, bounce, pulled)
+        for w in range(4):
+            if thermal_wall[w] == 1:
+                geq_w = geq_wall[w][i]
+                sel = (ox | oy) & (wall == w)
+                res = np.where(sel, -bounce + 2.0 * geq_w, res)
+        out[i] = res
+    return out
+
+
+# --------------------------------------------------------------------------
+# Solid fraction (Sec. 2, reading R1).
+# --------------------------------------------------------------------------
+
+
+def _segment_integral(u, R):
+    """P(u) = integral_0^u sqrt(R^2 - t^2) dt for |u| <= R."""
+    u = np.clip(u, -R, R)
+    return 0.5 * (u * np.sqrt(np.maximum(R * R - u * u, 0.0)) + R * R * np.arcsin(u / R))
+
+
+def quadrant_area(a, b, R):
+    """Area of {(u, v): u^2 + v^2 <= R^2, u <= a, v <= b} (disk at origin).
+
+    For fixed u the admissible v form [-s, min(b, s)], s = sqrt(R^2 - u^2).
+    Its length is 2s where s <= b, b + s where -s < b < s, and 0 where
+    b <= -s.  With c = sqrt(R^2 - b^2) those regions are |u| >= c (b >= 0),
+    |u| < c, and |u| >= c (b < 0); integrating them up to u = a gives the
+    result."""
+    a = np.clip(np.asarray(a, dtype=np.float64), -R, R)
+    b = np.clip(np.asarray(b, dtype=np.float64), -R, R)
+    c = np.sqrt(np.maximum(R * R - b * b, 0.0))
+    P = lambda u: _segment_integral(u, R)  # noqa: E731
+    # u in [-R, -c]: length 2s if b >= 0 else 0
+    hi1 = np.minimum(a, -c)
+    seg1 = np.where((b >= 0) & (hi1 > -R), 2.0 * (P(hi1) - P(-R)), 0.0)
+    # u in [-c, c]: length b + s
+    hi2 = np.minimum(a, c)
+    seg2 = np.where(hi2 > -c, b * (hi2 + c) + P(hi2) - P(-c), 0.0)
+    # u in [c, R]: length 2s if b >= 0 else 0
+    seg3 = np.where((b >= 0) & (a > c), 2.0 * (P(a) - P(c)), 0.0)
+    return seg1 + seg2 + seg3
+
+
+def cell_disk_area(x0, x1, y0, y1, X, Y, R):
+    """Exact area of disk(X, Y, R) ∩ [x0, x1] x [y0, y1] by inclusion-exclusion
+    of quadrant areas."""
+    a0, a1 = x0 - X, x1 - X
+    b0, b1 = y0 - Y, y1 - Y
+    return (quadrant_area(a1, b1, R) - quadrant_area(a0, b1, R)
+            - quadrant_area(a1, b0, R) + quadrant_area(a0, b0, R))
+
+
+def quantise(v) -> np.ndarray:
+    """Round to the 2^-20 fixed-point grid of the integer cell tests."""
+    return np.rint(np.asarray(v, dtype=np.float64) * float(1 << QBITS)).astype(np.int64)
+
+
+FLUID, INTERFACE, SOLID = 0, 1, 2
+
+
+def cell_flags(i, j, Xq, Yq, Rq):
+    """Classify cells (i, j) against one disk in fixed point (reading R1):
+    SOLID if all four corners are in the closed disk, FLUID if the nearest
+    point of the cell is at distance >= R, INTERFACE otherwise."""
+    Q = np.int64(1 << QBITS)
+    cx0 = i.astype(np.int64) * Q - Xq
+    cx1 = cx0 + Q
+    cy0 = j.astype(np.int64) * Q - Yq
+    cy1 = cy0 + Q
+    far2 = np.maximum(cx0 * cx0, cx1 * cx1) + np.maximum(cy0 * cy0, cy1 * cy1)
+    nx_ = np.where((cx0 <= 0) & (cx1 >= 0), 0, np.minimum(np.abs(cx0), np.abs(cx1)))
+    ny_ = np.where((cy0 <= 0) & (cy1 >= 0), 0, np.minimum(np.abs(cy0), np.abs(cy1)))
+    near2 = nx_ * nx_ + ny_ * ny_
+    R2 = Rq * Rq
+    return np.where(far2 <= R2, SOLID, np.where(near2 >= R2, FLUID, INTERFACE))
+
+
+@dataclasses.dataclass
+class Raster:
+    """Per-cell solid fraction and ownership (reading R1)."""
+    fs: np.ndarray         # (ny, nx) total solid fraction
+    count: np.ndarray      # (ny, nx) number of owners
+    owner: np.ndarray      # (ny, nx, 4) particle id, -1 padded, ascending
+    flag: np.ndarray       # (ny, nx, 4) INTERFACE or SOLID, 0 padded
+    fsp: np.ndarray        # (ny, nx, 4) per-owner fraction (after scaling)
+
+
+def rasterise(nx, ny, X, Y, R) -> Raster:
+    """Solid-fraction field f_s of a set of disks (Sec. 2 and Eq. 8)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    R = np.asarray(R, dtype=np.float64)
+    count = np.zeros((ny, nx), dtype=np.int64)
+    owner = np.full((ny, nx, MAX_OWNERS), -1, dtype=np.int64)
+    flag = np.zeros((ny, nx, MAX_OWNERS), dtype=np.int64)
+    fsp = np.zeros((ny, nx, MAX_OWNERS), dtype=np.float64)
+    Xq, Yq, Rq = quantise(X), quantise(Y), quantise(R)
+    for p in range(X.shape[0]):
+        i0 = max(int(math.floor(X[p] - R[p])) - 1, 0)
+        i1 = min(int(math.ceil(X[p] + R[p])) + 1, nx - 1)
+        j0 = max(int(math.floor(Y[p] - R[p])) - 1, 0)
+        j1 = min(int(math.ceil(Y[p] + R[p])) + 1, ny - 1)
+        if i1 < i0 or j1 < j0:
+            continue
+        jj, ii = np.meshgrid(np.arange(j0, j1 + 1), np.arange(i0, i1 + 1), indexing="ij")
+        fl = cell_flags(ii, jj, Xq[p], Yq[p], Rq[p])
+        sel = fl != FLUID
+        if not sel.any():
+            continue
+        ci, cj, cf = ii[sel], jj[sel], fl[sel]
+        area = cell_disk_area(ci.astype(float), ci + 1.0, cj.astype(float), cj + 1.0, X[p], Y[p], R[p])
+        val = np.where(cf == SOLID, 1.0, np.clip(area, 0.0, 1.0))
+        k = count[cj, ci]
+        if (k >= MAX_OWNERS).any():
+            raise OverflowError("more than 4 particles own one cell")
+        owner[cj, ci, k] = p
+        flag[cj, ci, k] = cf
+        fsp[cj, ci, k] = val
+        count[cj, ci] = k + 1
+    tot = fsp.sum(axis=2)
+    scale = np.where(tot > 1.0, 1.0 / np.where(tot > 1.0, tot, 1.0), 1.0)
+    fsp = fsp * scale[:, :, None]
+    return Raster(fs=fsp.sum(axis=2), count=count, owner=owner, flag=flag, fsp=fsp)
+
+
+# --------------------------------------------------------------------------
+# Volumetric correction and momentum exchange (Eqs. 8, 27, 28).
+# --------------------------------------------------------------------------
+
+
+def solid_velocity(xc, yc, Ux, Uy, Om, Xc, Yc):
+    """Rigid-body velocity u_s(x) = U_c + Omega_c x (x - X_c) of Eq. 27 (2-D)."""
+    return Ux - Om * (yc - Yc), Uy + Om * (xc - Xc)
+
+
+def correct_and_exchange(fstar, ras: Raster, part):
+    """Eq. 8 with several owners,
+         f = (1 - sum_p f_s,p) f* + sum_p f_s,p f^eq(rho, u_s,p),
+    rho = sum f*, and the per-particle force and torque of Eq. 28,
+         F_p = - sum_x f_s,p sum_i [f_i^eq(rho, u_s,p) - f*_i] e_i,
+         T_p = - sum_x (x - X_p) x f_s,p sum_i [f_i^eq - f*_i] e_i.
+    Returns f, F (n, 2), T (n,)."""
+    _, ny, nx = fstar.shape
+    n = part["x"].shape[0]
+    rho = fstar.sum(axis=0)
+    f = (1.0 - ras.fs)[None] * fstar
+    F = np.zeros((n, 2))
+    T = np.zeros(n)
+    for k in range(MAX_OWNERS):
+        cj, ci = np.nonzero(ras.count > k)
+        if cj.size == 0:
+            continue
+        p = ras.owner[cj, ci, k]
+        w = ras.fsp[cj, ci, k]
+        xc, yc = ci + 0.5, cj + 0.5
+        usx, usy = solid_velocity(xc, yc, part["ux"][p], part["uy"][p], part["omega"][p],
+                                  part["x"][p], part["y"][p])
+        fe = feq(rho[cj, ci], usx, usy)                       # (9, ncell)
+        f[:, cj, ci] += w[None] * fe
+        d = fe - fstar[:, cj, ci]
+        dFx = -w * np.tensordot(EX, d, axes=(0, 0))
+        dFy = -w * np.tensordot(EY, d, axes=(0, 0))
+        dT = (xc - part["x"][p]) * dFy - (yc - part["y"][p]) * dFx
+        F[:, 0] += np.bincount(p, weights=dFx, minlength=n)
+        F[:, 1] += np.bincount(p, weights=dFy, minlength=n)
+        T += np.bincount(p, weights=dT, minlength=n)
+    return f, F, T
+
+
+# --------------------------------------------------------------------------
+# Thermal LBE (Sec. 2.2): Eqs. 11, 17-25.
+# --------------------------------------------------------------------------
+
+
+def reference_cv(cv_f: float, cv_s: float) -> float:
+    """c_v,ref: harmonic mean of the two specific heats (Sec. 2.2)."""
+    return 2.0 * cv_f * cv_s / (cv_f + cv_s)
+
+
+def thermal_eq_moments(eps, T, cref):
+    """n^eq(eps, T) of Eq. 19."""
+    z = np.zeros_like(eps * T)
+    return np.stack([eps + z, -4.0 * eps + (4.0 + ALPHA1) * cref * T,
+                     4.0 * eps - (4.0 - ALPHA2) * cref * T, z, z, z, z, z, z])
+
+
+def source_moments(qc):
+    """q_m of Eq. 20."""
+    z = np.zeros_like(qc)
+    return np.stack([qc, BETA1 * qc, BETA2 * qc, z, z, z, z, z, z])
+
+
+def geq(eps, T, cref):
+    """g^eq = M^-1 n^eq(eps, T) (definition below Eq. 18)."""
+    return from_moments(thermal_eq_moments(eps, T, cref))
+
+
+def tau_g_of(lam, cref, rho_f=1.0):
+    """tau_g from Eq. 22: lambda / rho_f = (4 + alpha1)/6 c_ref (tau_g - 1/2)."""
+    return 0.5 + 6.0 * lam / ((4.0 + ALPHA1) * rho_f * cref)
+
+
+def thermal_rates(tau_g, mode: int = 0):
+    """Diagonal of R (Eq. 18) per cell.  Sec. 3: sigma_0 = 1,
+    sigma_eps = sigma_e, sigma_q = sigma_j = 1/tau_g and
+    (1/sigma_j - 1/2)(1/sigma_e - 1/2) = 1/4 (mode 0); Sec. 3.5:
+    sigma_0 = sigma_eps = sigma_e = 1 (mode 1)."""
+    sj = 1.0 / tau_g
+    if mode == 0:
+        se = 1.0 / (0.5 + 0.25 / (tau_g - 0.5))
+    else:
+        se = np.ones_like(tau_g)
+    one = np.ones_like(tau_g)
+    return np.stack([one, se, se, sj, sj, sj, sj, se, se])
+
+
+def collide_thermal(g, eps, T, qc, Rdiag, cref):
+    """Post-collision gbar from Eq. 17a:
+    nbar = n - R (n - n^eq) + (I - R/2) q_m."""
+    n = to_moments(g)
+    neq = thermal_eq_moments(eps, T, cref)
+    qm = source_moments(qc)
+    nbar = n - Rdiag * (n - neq) + (1.0 - 0.5 * Rdiag) * qm
+    return from_moments(nbar)
+
+
+def dfs_dt_update(fs_new, fs_old, dfs_old):
+    """[df_s/dt](t + dt) = 2 (f_s(t + dt) - f_s(t)) - [df_s/dt](t)  (Eq. 24)."""
+    return 2.0 * (fs_new - fs_old) - dfs_old
+
+
+def temperature_gradient(g, cref, tau_g):
+    """Local gradient scheme of Eq. 23:
+    grad T = -6/(4 + alpha1) * sum_i e_i g_i / (c_ref tau_g)."""
+    k = -6.0 / (4.0 + ALPHA1)
+    gx = k * np.tensordot(EX, g, axes=(0, 0)) / (cref * tau_g)
+    gy = k * np.tensordot(EY, g, axes=(0, 0)) / (cref * tau_g)
+    return gx, gy
+
+
+def temperature_prescribed_u(G, cv, cv_f, cv_s, dfs, ux, uy, gTx, gTy):
+    """Eq. 25 with a given velocity field:
+    T = (sum g - 1/2 c_v u.grad T) / (c_v - 1/2 (c_vs - c_vf) df_s/dt)."""
+    return (G - 0.5 * cv * (ux * gTx + uy * gTy)) / (cv - 0.5 * (cv_s - cv_f) * dfs)
+
+
+def temperature_and_velocity(G, cv, cv_f, cv_s, dfs, rho, jx, jy, fs, bx, by, T_ref, gTx, gTy):
+    """Eq. 25 solved jointly with Eq. 9 when the buoyancy force
+    F = (1 - f_s) b (T - T_ref), b = -rho_f beta g, depends on T (reading R4).
+
+    With u = u0 + a (T - T_ref), u0 = j/rho, a = (1 - f_s) b / (2 rho),
+    Eq. 25 reads T D = G - 1/2 c_v (u0 + a (T - T_ref)).grad T with
+    D = c_v - 1/2 (c_vs - c_vf) df_s/dt, which is linear in T."""
+    D = cv - 0.5 * (cv_s - cv_f) * dfs
+    u0x, u0y = jx / rho, jy / rho
+    ax, ay = (1.0 - fs) * bx / (2.0 * rho), (1.0 - fs) * by / (2.0 * rho)
+    num = G - 0.5 * cv * ((u0x - ax * T_ref) * gTx + (u0y - ay * T_ref) * gTy)
+    den = D + 0.5 * cv * (ax * gTx + ay * gTy)
+    T = num / den
+    ux = u0x + ax * (T - T_ref)
+    uy = u0y + ay * (T - T_ref)
+    Fx = (1.0 - fs) * bx * (T - T_ref)
+    Fy = (1.0 - fs) * by * (T - T_ref)
+    return T, ux, uy, Fx, Fy
+
+
+def source_term(cv, cv_f, cv_s, ux, uy, gTx, gTy, T, dfs):
+    """q_c = -c_v u.grad T + (c_vs - c_vf) T df_s/dt (Eq. 16)."""
+    return -cv * (ux * gTx + uy * gTy) + (cv_s - cv_f) * T * dfs
+
+
+# --------------------------------------------------------------------------
+# Particle dynamics (Sec. 2.3): Eqs. 26, 29, 30 and contact (reading R5).
+# --------------------------------------------------------------------------
+
+
+def contact_pairs(X, Y, R, zeta):
+    """All pairs i < j with d_ij < R_i + R_j + zeta, ascending (brute force)."""
+    n = len(X)
+    pairs = []
+    for i in range(n):
+        for j in range(i + 1, n):
+            dx = X[i] - X[j]
+            dy = Y[i] - Y[j]
+            thr = R[i] + R[j] + zeta
+            if dx * dx + dy * dy < thr * thr:
+                pairs.append((i, j))
+    return pairs
+
+
+def contact_forces(X, Y, R, prm, pairs):
+    """Contact force on each particle (reading R5); partners are summed in
+    ascending id, then walls x-, x+, y-, y+."""
+    n = len(X)
+    zeta = prm.contact_range
+    gmag = math.hypot(prm.gravity[0], prm.gravity[1])
+    scale = abs(prm.rho_ratio - 1.0) * 1.0 * gmag * math.pi
+    partners = [[] for _ in range(n)]
+    for i, j in pairs:
+        partners[i].append(j)
+        partners[j].append(i)
+    F = np.zeros((n, 2))
+    for i in range(n):
+        for j in sorted(partners[i]):
+            dx = X[i] - X[j]
+            dy = Y[i] - Y[j]
+            d = math.sqrt(dx * dx + dy * dy)
+            gap = R[i] + R[j] + zeta - d
+            if gap <= 0.0:
+                continue
+            c = scale * max(R[i], R[j]) ** 2
+            mag = (c / prm.contact_eps_p) * (gap / zeta) ** 2 / d
+            F[i, 0] += mag * dx
+            F[i, 1] += mag * dy
+        c = scale * R[i] ** 2
+        walls = [(0, X[i] - 0.0, 1.0, 0.0), (0, prm.nx - X[i], -1.0, 0.0),
+                 (1, Y[i] - 0.0, 0.0, 1.0), (1, prm.ny - Y[i], 0.0, -1.0)]
+        for axis, dist, nxw, nyw in walls:
+            if prm.periodic[axis]:
+                continue
+            d = 2.0 * dist
+            gap = 2.0 * R[i] + zeta - d
+            if gap <= 0.0:
+                continue
+            mag = (c / prm.contact_eps_w) * (gap / zeta) ** 2
+            F[i, 0] += mag * nxw
+            F[i, 1] += mag * nyw
+    return F
+
+
+# --------------------------------------------------------------------------
+# Parameters and the coupled time step.
+# --------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Params:
+    """Problem statement in lattice units (Sec. 3; rho_f = c_vf = 1)."""
+    nx: int
+    ny: int
+    tau_f: float = 0.8
+    lambda_q_flow: float = 1.0 / 12.0
+    s_e: float = 1.25
+    prandtl: float = 0.7
+    rho_ratio: float = 1.5
+    cv_ratio: float = 1.0
+    k_ratio_default: float = 1.0
+    gravity: tuple = (0.0, 0.0)
+    beta: float = 0.0
+    T_ref: float = 1.0
+    T_fluid_init: float = 1.0
+    thermal_wall: tuple = (0, 0, 0, 0)   # 0 adiabatic, 1 held at wall_T
+    wall_T: tuple = (0.0, 0.0, 0.0, 0.0)
+    thermal_rates_mode: int = 0
+    contact_range: float = 2.0
+    contact_eps_p: float = 0.01
+    contact_eps_w: float = 0.005
+    periodic: tuple = (False, False)
+
+    # derived quantities (Sec. 3)
+    @property
+    def nu(self):
+        return (self.tau_f - 0.5) / 3.0
+
+    @property
+    def cv_f(self):
+        return 1.0
+
+    @property
+    def cv_s(self):
+        return self.cv_ratio
+
+    @property
+    def lambda_f(self):
+        return 1.0 * self.cv_f * self.nu / self.prandtl
+
+    @property
+    def cref(self):
+        return reference_cv(self.cv_f, self.cv_s)
+
+
+class Simulation:
+    """The coupled step of Sec. 2, phase by phase.
+
+    State at level n: post-correction f, g; rho, u, F, T, eps, q_c; f_s^n
+    with its owners; [df_s/dt]^n; per particle X, theta, U, Omega, the
+    previous U, Omega and the hydrodynamic force and torque of level n."""
+
+    def __init__(self, prm: Params, x, y, radius, T0, k_ratio=None, ux=None, uy=None, omega=None):
+        self.prm = prm
+        n = len(x)
+        z = np.zeros(n)
+        self.part = {
+            "x": np.array(x, dtype=float), "y": np.array(y, dtype=float),
+            "r": np.array(radius, dtype=float), "T0": np.array(T0, dtype=float),
+            "k": np.array(k_ratio if k_ratio is not None else np.full(n, prm.k_ratio_default), dtype=float),
+            "ux": np.array(ux if ux is not None else z, dtype=float),
+            "uy": np.array(uy if uy is not None else z, dtype=float),
+            "omega": np.array(omega if omega is not None else z, dtype=float),
+            "theta": np.zeros(n),
+        }
+        self.part["ux_prev"] = self.part["ux"].copy()
+        self.part["uy_prev"] = self.part["uy"].copy()
+        self.part["omega_prev"] = self.part["omega"].copy()
+        r = self.part["r"]
+        self.mass = prm.rho_ratio * math.pi * r * r           # M
+        self.inertia = 0.5 * self.mass * r * r                 # I_c (disk)
+        self.mass_in = 1.0 * math.pi * r * r                   # M_in = rho_f M / rho_s
+        self.inertia_in = 0.5 * self.mass_in * r * r           # I_c,in
+        self.S = flow_rates(prm.tau_f, prm.lambda_q_flow, prm.s_e)
+        self.b = (-1.0 * prm.beta * prm.gravity[0], -1.0 * prm.beta * prm.gravity[1])
+        self.step_count = 0
+        self._init_state()
+
+    # -- helpers ------------------------------------------------------------
+    def _properties(self, ras: Raster):
+        """c_v and lambda of Eq. 11, summed over owners."""
+        p = self.prm
+        cv = (1.0 - ras.fs) * p.cv_f
+        lam = (1.0 - ras.fs) * p.lambda_f
+        for k in range(MAX_OWNERS):
+            sel = ras.count > k
+            if not sel.any():
+                continue
+            w = np.where(sel, ras.fsp[:, :, k], 0.0)
+            kp = self.part["k"][np.where(sel, ras.owner[:, :, k], 0)]
+            cv = cv + w * p.cv_s
+            lam = lam + w * kp * p.lambda_f
+        return cv, lam
+
+    def _raster(self):
+        p = self.prm
+        return rasterise(p.nx, p.ny, self.part["x"], self.part["y"], self.part["r"])
+
+    def _init_state(self):
+        """Initial state (reading R6)."""
+        p = self.prm
+        ny, nx = p.ny, p.nx
+        self.ras = self._raster()
+        ones = np.ones((ny, nx))
+        fstar = feq(ones, 0.0 * ones, 0.0 * ones)
+        self.f, self.F_mes, self.T_mes = correct_and_exchange(fstar, self.ras, self.part)
+        self.cv, lam = self._properties(self.ras)
+        self.tau_g = tau_g_of(lam, p.cref)
+        eps = (1.0 - self.ras.fs) * p.cv_f * p.T_fluid_init
+        for k in range(MAX_OWNERS):
+            sel = self.ras.count > k
+            if sel.any():
+                Tp = self.part["T0"][np.where(sel, self.ras.owner[:, :, k], 0)]
+                eps = eps + np.where(sel, self.ras.fsp[:, :, k], 0.0) * p.cv_s * Tp
+        self.eps = eps
+        self.T = eps / self.cv
+        self.qc = np.zeros((ny, nx))
+        self.dfs = np.zeros((ny, nx))
+        self.g = geq(self.eps, self.T, p.cref)
+        rho = self.f.sum(axis=0)
+        jx = np.tensordot(EX, self.f, axes=(0, 0))
+        jy = np.tensordot(EY, self.f, axes=(0, 0))
+        self.Fx = (1.0 - self.ras.fs) * self.b[0] * (self.T - p.T_ref)
+        self.Fy = (1.0 - self.ras.fs) * self.b[1] * (self.T - p.T_ref)
+        self.rho = rho
+        self.ux = (jx + 0.5 * self.Fx) / rho
+        self.uy = (jy + 0.5 * self.Fy) / rho
+        self.Fc = np.zeros((len(self.part["x"]), 2))
+        self.Tc = np.zeros(len(self.part["x"]))
+        self.pairs = contact_pairs(self.part["x"], self.part["y"], self.part["r"], p.contact_range)
+
+    def _particle_update(self):
+        """Eqs. 26, 29, 30 by forward Euler with backward differences for
+        dU/dt and dOmega/dt in F_in, T_in (end of Sec. 2.3)."""
+        p = self.prm
+        P = self.part
+        r = P["r"]
+        Fcon = contact_forces(P["x"], P["y"], r, p, self.pairs)
+        body = (p.rho_ratio - 1.0) * 1.0 * math.pi * r * r
+        F_in_x = -self.mass_in * (P["ux"] - P["ux_prev"])
+        F_in_y = -self.mass_in * (P["uy"] - P["uy_prev"])
+        T_in = -self.inertia_in * (P["omega"] - P["omega_prev"])
+        Fcx = self.F_mes[:, 0] - F_in_x + body * p.gravity[0] + Fcon[:, 0]
+        Fcy = self.F_mes[:, 1] - F_in_y + body * p.gravity[1] + Fcon[:, 1]
+        Tc = self.T_mes - T_in
+        self.Fc = np.stack([Fcx, Fcy], axis=1)
+        self.Tc = Tc
+        ux_new = P["ux"] + Fcx / self.mass
+        uy_new = P["uy"] + Fcy / self.mass
+        om_new = P["omega"] + Tc / self.inertia
+        P["x"] = P["x"] + P["ux"]
+        P["y"] = P["y"] + P["uy"]
+        P["theta"] = P["theta"] + P["omega"]
+        P["ux_prev"], P["uy_prev"], P["omega_prev"] = P["ux"], P["uy"], P["omega"]
+        P["ux"], P["uy"], P["omega"] = ux_new, uy_new, om_new
+
+    def step(self, nsteps: int = 1):
+        for _ in range(nsteps):
+            self._step()
+
+    def _step(self):
+        p = self.prm
+        # (1) collisions at level n (Eqs. 3a, 17a)
+        fbar = collide_flow(self.f, self.rho, self.ux, self.uy, self.Fx, self.Fy, self.S)
+        Rd = thermal_rates(self.tau_g, p.thermal_rates_mode)
+        gbar = collide_thermal(self.g, self.eps, self.T, self.qc, Rd, p.cref)
+        # (2) streaming (Eqs. 3b, 17b)
+        fstar = stream_flow(fbar, p.periodic)
+        g = stream_thermal(gbar, p.cref, p.thermal_wall, p.wall_T, p.periodic)
+        # (3) particle motion to level n+1 (reading R3), then f_s^{n+1}
+        self._particle_update()
+        fs_old = self.ras.fs
+        self.ras = self._raster()
+        # (4) volumetric correction and momentum exchange (Eqs. 8, 28)
+        self.f, self.F_mes, self.T_mes = correct_and_exchange(fstar, self.ras, self.part)
+        # (5) thermal macroscopics at n+1 (Eqs. 11, 21-25) jointly with rho, u (Eq. 9)
+        self.dfs = dfs_dt_update(self.ras.fs, fs_old, self.dfs)
+        self.cv, lam = self._properties(self.ras)
+        self.tau_g = tau_g_of(lam, p.cref)
+        gTx, gTy = temperature_gradient(g, p.cref, self.tau_g)
+        G = g.sum(axis=0)
+        rho = self.f.sum(axis=0)
+        jx = np.tensordot(EX, self.f, axes=(0, 0))
+        jy = np.tensordot(EY, self.f, axes=(0, 0))
+        T, ux, uy, Fx, Fy = temperature_and_velocity(
+            G, self.cv, p.cv_f, p.cv_s, self.dfs, rho, jx, jy, self.ras.fs,
+            self.b[0], self.b[1], p.T_ref, gTx, gTy)
+        self.g = g
+        self.rho, self.ux, self.uy, self.Fx, self.Fy, self.T = rho, ux, uy, Fx, Fy, T
+        self.eps = self.cv * T
+        self.qc = source_term(self.cv, p.cv_f, p.cv_s, ux, uy, gTx, gTy, T, self.dfs)
+        self.pairs = contact_pairs(self.part["x"], self.part["y"], self.part["r"], p.contact_range)
+        self.step_count += 1
+
+    # -- outputs -------------------------------------------------------------
+    def fields(self):
+        return {"rho": self.rho, "ux": self.ux, "uy": self.uy, "T": self.T, "fs": self.ras.fs}
+
+    def particle_state(self):
+        P = self.part
+        return {"x": P["x"].copy(), "y": P["y"].copy(), "theta": P["theta"].copy(),
+                "ux": P["ux"].copy(), "uy": P["uy"].copy(), "omega": P["omega"].copy(),
+                "fx": self.Fc[:, 0].copy(), "fy": self.Fc[:, 1].copy(), "torque": self.Tc.copy()}
+
+    def audit(self):
+        """Total mass sum f, total internal energy sum eps and sum g."""
+        return float(self.f.sum()), float(self.eps.sum()), float(self.g.sum())
+
+
+class PrescribedFlowThermal:
+    """The thermal LBE of Sec. 2.2 on its own, with the velocity field and
+    the solid fraction given in advance (the setting of Sec. 3.1, where
+    "only the LB equation for temperature field is involved").
+
+    ``fs_of(t)`` returns the solid-fraction field at time t; the velocity is
+    uniform.  Properties follow Eq. 11 with c_vf = 1, lambda_s = R_lambda
+    lambda_f, c_vs = R_cv."""
+
+    def __init__(self, nx, ny, lambda_f, R_lambda, R_cv, fs_of, T_solid, T_fluid, velocity=(0.0, 0.0),
+                 thermal_wall=(0, 0, 0, 0), wall_T=(0.0, 0.0, 0.0, 0.0), periodic=(False, True), mode=0):
+        self.nx, self.ny = nx, ny
+        self.lambda_f, self.lambda_s = lambda_f, R_lambda * lambda_f
+        self.cv_f, self.cv_s = 1.0, R_cv
+        self.cref = reference_cv(self.cv_f, self.cv_s)
+        self.fs_of = fs_of
+        self.u = velocity
+        self.walls, self.wall_T, self.periodic, self.mode = thermal_wall, wall_T, periodic, mode
+        self.t = 0
+        self.fs = fs_of(0)
+        self.dfs = np.zeros((ny, nx))
+        self.cv, self.tau_g = self._props(self.fs)
+        self.T = np.where(self.fs > 0.5, T_solid, T_fluid) * np.ones((ny, nx))
+        self.eps = self.cv * self.T
+        self.qc = np.zeros((ny, nx))
+        self.g = geq(self.eps, self.T, self.cref)
+
+    def _props(self, fs):
+        cv = (1.0 - fs) * self.cv_f + fs * self.cv_s
+        lam = (1.0 - fs) * self.lambda_f + fs * self.lambda_s
+        return cv, tau_g_of(lam, self.cref)
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            Rd = thermal_rates(self.tau_g, self.mode)
+            gbar = collide_thermal(self.g, self.eps, self.T, self.qc, Rd, self.cref)
+            g = stream_thermal(gbar, self.cref, self.walls, self.wall_T, self.periodic)
+            self.t += 1
+            fs_new = self.fs_of(self.t)
+            self.dfs = dfs_dt_update(fs_new, self.fs, self.dfs)
+            self.fs = fs_new
+            self.cv, self.tau_g = self._props(fs_new)
+            gTx, gTy = temperature_gradient(g, self.cref, self.tau_g)
+            ux = np.full_like(fs_new, self.u[0])
+            uy = np.full_like(fs_new, self.u[1])
+            self.T = temperature_prescribed_u(g.sum(axis=0), self.cv, self.cv_f, self.cv_s, self.dfs,
+                                              ux, uy, gTx, gTy)
+            self.eps = self.cv * self.T
+            self.qc = source_term(self.cv, self.cv_f, self.cv_s, ux, uy, gTx, gTy, self.T, self.dfs)
+            self.g = g
+
+
+def slab_fraction(nx, ny, X_interface):
+    """f_s of a solid filling x < X_interface (one-dimensional slab)."""
+    i = np.arange(nx, dtype=np.float64)
+    return np.broadcast_to(np.clip(X_interface - i, 0.0, 1.0), (ny, nx)).copy()
+
+
+def conjugate_erfc(x, t, X_i, T_h, T_c, lambda_f, R_lambda, R_cv):
+    """Closed form of the 1-D transient conjugate problem, Eq. 31 (solid at
+    x < X_i initially at T_h, fluid initially at T_c, rho_f = c_vf = 1)."""
+    a_s = R_lambda * lambda_f / R_cv
+    a_f = lambda_f / 1.0
+    e = math.sqrt(R_lambda * R_cv)
+    x = np.asarray(x, dtype=np.float64)
+    erfc = np.vectorize(math.erfc)
+    solid = T_h + (T_c - T_h) / (e + 1.0) * erfc((X_i - x) / (2.0 * math.sqrt(a_s * t)))
+    fluid = T_c + (T_h - T_c) * e / (e + 1.0) * erfc((x - X_i) / (2.0 * math.sqrt(a_f * t)))
+    return np.where(x < X_i, solid, fluid)
