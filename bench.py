@@ -1,0 +1,358 @@
+"""Throughput of the coupled flow + thermal + particle step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default): 2048 cold disks (D = 16 lu) in a 2048 x 2048 cavity, FP32
+(the seeded synthetic case of paper_2410_23802_gb300.workloads.cavity).  One
+step is one full pass of the hot path: particle update and contacts, solid
+fraction, f and g collide/stream with the volumetric correction, MES partial
+sums.  Metric: coupled MLUPS (one lattice update = f and g at one cell).
+Under torchrun each rank runs its own replica of the case on its GPU (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"fp32": 152, "fp64": 304}  # f and g read + write, S read + write
+METRIC = "coupled flow+thermal MLUPS"
+UNIT = "MLUPS"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2410_23802_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(workload_key):
+    """DRAM bytes per lattice launch from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "lattice_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        ent = rec.get(workload_key)
+        if ent and ent.get("source_hash") == _source_hash():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _make_case(args):
+    from paper_2410_23802_gb300 import workloads as W
+    return W.cavity(side=args.side, n=args.particles, precision=args.precision)
+
+
+def _params(case, V):
+    prm = {k: v for k, v in case.params.items() if k != "precision"}
+    prec = V.VLB_FP64 if case.params["precision"] == "fp64" else V.VLB_FP32
+    return V.vlb_params_default(precision=prec, max_particles=len(case.x), **prm)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2410_23802_gb300 import vlb as V
+
+    case = _make_case(args)
+    cells = case.cells
+    stream = torch.cuda.Stream()
+    xy = np.column_stack([case.x, case.y])
+
+    # ---- device-resident throughput ------------------------------------------
+    lat = V.Lattice(_params(case, V))
+    V.vlb_set_stream(lat.h, stream.cuda_stream)
+    lat.add_particles(xy, case.radius, case.T0, k_ratio=case.k_ratio)
+    with torch.cuda.stream(stream):
+        lat.step(args.warmup)
+        V.vlb_synchronize(lat.h)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        V.vlb_profile_begin(lat.h, args.steps)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        lat.step(args.steps)
+        t1.record(stream)
+        V.vlb_synchronize(lat.h)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    lattice_ms, lattice_launches, launches_per_step = V.vlb_profile_end(lat.h)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        torch.distributed.barrier()
+    lat.close()
+
+    # ---- end to end through the public API with host buffers -------------------
+    e2e_steps = args.steps
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    w0 = time.perf_counter()
+    lat2 = V.Lattice(_params(case, V))
+    lat2.add_particles(xy, case.radius, case.T0, k_ratio=case.k_ratio)
+    lat2.step(e2e_steps)
+    fields = lat2.fields()
+    parts = lat2.particles()
+    V.vlb_synchronize(lat2.h)
+    e2e_s = time.perf_counter() - w0
+    lat2.close()
+    assert np.isfinite(fields["T"]).all() and np.isfinite(parts["y"]).all()
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = len(case.x) * (2 * 8 + 3 * 8)          # centres, radius, T0, k_ratio
+    d2h = cells * 5 * 8 + len(case.x) * 9 * 8   # five fields and the particle state, FP64
+
+    if rank != 0:
+        return
+    value = world * cells * args.steps / (elapsed_ms * 1e-3) / 1e6
+    peak, peak_kind = _peaks()
+    lattice_avg_s = lattice_ms * 1e-3 / max(lattice_launches, 1)
+    bpc = BYTES_PER_CELL[args.precision]
+    achieved = bpc * cells / lattice_avg_s / 1e9
+    key = f"cavity{args.side}_{args.particles}_{args.precision}"
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded SplitMix64 placement)",
+        "config": {"workload": case.name, "cells": cells, "particles": len(case.x),
+                   "storage": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2: {cells * bpc / 2 / 1e6:.0f} MB of lattice state per step"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(key),
+                     "kernel": "lattice_kernel<STEP>", "bytes_per_cell": bpc, "peak_kind": peak_kind,
+                     "avg_launch_us": round(lattice_avg_s * 1e6, 2)},
+        "e2e": {"value": round(world * cells * e2e_steps / e2e_s / 1e6, 1), "unit": UNIT,
+                "h2d_bytes_per_step": round(h2d / e2e_steps, 1), "d2h_bytes_per_step": round(d2h / e2e_steps, 1),
+                "note": "create + host particle upload + steps + fields and particle state to host, wall clock"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, budget_s=15.0)
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+
+def _crop_case(args, side):
+    """The cavity workload restricted to a side x side window at its top
+    centre (same parameters, the disks lying inside the window)."""
+    from paper_2410_23802_gb300 import workloads as W
+    full = _make_case(args)
+    x0 = (args.side - side) // 2
+    y0 = args.side - side
+    xs, ys, rs, ts = [], [], [], []
+    for x, y, r, t in zip(full.x, full.y, full.radius, full.T0):
+        if x - r - 2 >= x0 and x + r + 2 <= x0 + side and y - r - 2 >= y0 and y + r + 2 <= y0 + side:
+            xs.append(x - x0); ys.append(y - y0); rs.append(r); ts.append(t)
+    prm = dict(full.params)
+    prm["nx"] = prm["ny"] = side
+    return W.Case(f"{side}x{side} window of {full.name}", prm, xs, ys, rs, ts)
+
+
+_CPU_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import vlbref as O
+from paper_2410_23802_gb300 import workloads as W
+spec = json.loads({spec!r})
+case = W.Case(**spec["case"])
+prm = {{k: v for k, v in case.params.items() if k != "precision"}}
+sim = O.Simulation(O.Params(**prm), case.x, case.y, case.radius, case.T0)
+for _ in range(spec["warmup"]):
+    sim.step()
+times = []
+t_start = time.perf_counter()
+for _ in range(spec["steps"]):
+    t = time.perf_counter()
+    sim.step()
+    times.append(time.perf_counter() - t)
+    if spec["budget"] > 0 and time.perf_counter() - t_start > spec["budget"]:
+        break
+print(json.dumps({{"times": times}}))
+"""
+
+
+def _run_oracle(case, steps, warmup, budget):
+    import dataclasses
+    spec = {"case": dataclasses.asdict(case), "steps": steps, "warmup": warmup, "budget": budget}
+    spec["case"]["params"] = {k: (list(v) if isinstance(v, tuple) else v) for k, v in case.params.items()}
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _CPU_CHILD.format(root=ROOT, spec=json.dumps(spec))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])["times"]
+
+
+def cpu_baseline(args, budget_s):
+    side = min(512, args.side)
+    case = _crop_case(args, side)
+    times = _run_oracle(case, steps=1000, warmup=1, budget=budget_s)
+    per_step = sum(times) / len(times)
+    return {"value": round(case.cells / per_step / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} steps of the FP64 numpy oracle on the {case.name} "
+                      f"({len(case.x)} disks), 1 thread, after 1 untimed step"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    # size the window so that the K timed steps take about 60 s of CPU time
+    probe = _crop_case(args, 256)
+    t_probe = statistics.median(_run_oracle(probe, steps=3, warmup=1, budget=0))
+    per_cell = 1.5 * t_probe / probe.cells  # per-cell cost grows with the window
+    side = int((60.0 / max(args.steps, 1) / per_cell) ** 0.5)
+    side = max(64, min(args.side, side - side % 32))
+    case = _crop_case(args, side)
+    times = _run_oracle(case, steps=args.steps, warmup=min(args.warmup, 3), budget=0)
+    total = sum(times)
+    value = case.cells * len(times) / total / 1e6
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": len(times),
+        "warmup": min(args.warmup, 3),
+        "ms_per_step": round(1e3 * total / len(times), 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64 placement)",
+        "config": {"workload": _make_case(args).name, "sample": case.name, "particles": len(case.x),
+                   "storage": "fp64"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} steps on the {case.name}"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=2048)
+    ap.add_argument("--particles", type=int, default=2048)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * vlb.h -- C ABI of a GB300 (sm_103a) implementation of the volumetric
+ * lattice Boltzmann method for thermal particulate flows with conjugate heat
+ * transfer (Zhang, Wang, Li & Huang, arXiv 2410.23802).
+ *
+ * One time step (Sec. 2 of the paper) consists of
+ *   - the particle update (Eqs. 26, 29, 30; forward Euler) with contact forces,
+ *   - the solid fraction f_s of every cell from the particle positions (Sec. 2),
+ *   - collision and streaming of the flow populations f (Eqs. 3-7) followed by
+ *     the volumetric nonslip correction (Eq. 8) and the macroscopic rho, u (Eq. 9),
+ *   - the momentum-exchange force and torque on each particle (Eq. 28),
+ *   - collision and streaming of the internal-energy populations g (Eqs. 17-20)
+ *     with the convection term as a source (Eq. 16), variable c_v and lambda
+ *     (Eq. 11), the local temperature gradient (Eq. 23), the df_s/dt recursion
+ *     (Eq. 24) and the implicit temperature (Eq. 25).
+ *
+ * Units are lattice units (dx = dt = c = 1, rho_f = c_vf = 1).  The lattice has
+ * nx * ny cells; cell (i, j) covers [i, i+1] x [j, j+1] and its node sits at
+ * the cell centre.  Field arrays exchanged with the caller are row-major with
+ * y as the slow index: element (j, i) is at j * nx + i.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a vlb_status; no C++ exception crosses the ABI.
+ *   - All pointers are HOST pointers owned by the caller unless stated.  The
+ *     library owns all device memory of a handle and frees it in vlb_destroy.
+ *   - Work is queued on the handle's CUDA stream; vlb_step returns before the
+ *     GPU finishes.  The vlb_get_* calls synchronise that stream first.
+ *   - A handle is not thread-safe; separate handles are independent.
+ *   - On failure the call returns a negative status and vlb_last_error()
+ *     describes it; the handle stays usable unless the status is VLB_ECUDA.
+ *   - Device-side failures (list overflows, a particle leaving the domain or
+ *     moving faster than 0.5 lu per step, NaN) set a flag that the next call
+ *     returns as VLB_EOVERFLOW or VLB_EUNSTABLE; no kernel traps or spins.
+ */
+#ifndef VLB_H
+#define VLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VLB_ABI_VERSION 1u
+
+typedef struct vlb_handle vlb_handle;
+
+typedef enum {
+  VLB_OK = 0,
+  VLB_EINVAL = -1,     /* bad argument or parameter */
+  VLB_ENOMEM = -2,     /* device or host allocation failed */
+  VLB_ECUDA = -3,      /* a CUDA call failed; the handle should be destroyed */
+  VLB_ESTATE = -4,     /* call not allowed in the handle's current state */
+  VLB_EUNSTABLE = -5,  /* NaN, a particle too fast, or a particle out of the domain */
+  VLB_EOVERFLOW = -6,  /* a fixed-capacity list (owners, tile lists, contacts) overflowed */
+  VLB_ETIMEOUT = -7    /* reserved for bounded device-side waits */
+} vlb_status;
+
+/* Arithmetic and storage precision of the lattice populations. */
+typedef enum {
+  VLB_FP64 = 0,        /* FP64 storage and arithmetic */
+  VLB_FP32 = 1,        /* FP32 storage and arithmetic */
+  VLB_FP16_STORE = 2,  /* reserved: FP16 storage, FP32 arithmetic */
+  VLB_BF16_STORE = 3   /* reserved: BF16 storage, FP32 arithmetic */
+} vlb_precision;
+
+typedef enum { VLB_WALL_ADIABATIC = 0, VLB_WALL_DIRICHLET = 1 } vlb_thermal_wall;
+
+/* Field selection bits of vlb_get_fields. */
+enum {
+  VLB_FIELD_RHO = 1,
+  VLB_FIELD_UX = 2,
+  VLB_FIELD_UY = 4,
+  VLB_FIELD_T = 8,
+  VLB_FIELD_FS = 16
+};
+
+/*
+ * Problem statement (Sec. 3 of the paper; rho_f = c_vf = 1).  Fill it with
+ * vlb_params_default() and override fields.  Walls sit on the cell faces of
+ * every non-periodic side; they are no-slip (halfway bounce-back of f) and
+ * either adiabatic (bounce-back of g) or held at wall_T (anti-bounce-back).
+ * Side order in the [4] arrays: x-, x+, y-, y+.
+ */
+typedef struct {
+  uint32_t abi_version;       /* must equal VLB_ABI_VERSION */
+  int32_t nx, ny;             /* lattice cells, >= 2 each */
+  int32_t periodic[2];        /* 1 = periodic in x / y instead of walls */
+  int32_t thermal_wall[4];    /* vlb_thermal_wall per side */
+  int32_t thermal_rates_mode; /* 0: (1/s_j-1/2)(1/s_e-1/2)=1/4 (Sec. 3); 1: s_0=s_e=s_eps=1 (Sec. 3.5) */
+  int32_t precision;          /* vlb_precision */
+  int32_t max_particles;      /* capacity of the particle arrays */
+  int32_t reserved0, reserved1;  /* zero */
+  double tau_f;               /* flow relaxation time, s_p = 1/tau_f (Sec. 2.1) */
+  double lambda_q_flow;       /* (1/s_p-1/2)(1/s_q-1/2); the paper uses 1/12 (Sec. 3) */
+  double s_e;                 /* s_e = s_eps; the paper uses 1.25 (Sec. 3) */
+  double prandtl;             /* Pr = nu / alpha_f; sets lambda_f = nu / Pr */
+  double rho_ratio;           /* rho_s / rho_f, all particles */
+  double cv_ratio;            /* R_cv = c_vs / c_vf (pseudo specific heat, Sec. 2.2) */
+  double k_ratio_default;     /* R_lambda = lambda_s / lambda_f when none is given per particle */
+  double gravity[2];          /* gravitational acceleration g (lattice units) */
+  double beta;                /* volume expansivity; buoyancy -rho_f beta g (T - T_ref) on the fluid */
+  double T_ref;               /* buoyancy reference temperature */
+  double T_fluid_init;        /* initial fluid temperature */
+  double wall_T[4];           /* wall temperatures of Dirichlet sides */
+  double contact_range;       /* zeta of the short-range contact force (lu) */
+  double contact_eps_p;       /* stiffness parameter between particles */
+  double contact_eps_w;       /* stiffness parameter between a particle and a wall */
+} vlb_params;
+
+/* sizeof(vlb_params), for bindings that re-declare the struct. */
+size_t vlb_params_size(void);
+
+/* Fill *p with the paper's defaults: tau_f = 0.8, lambda_q_flow = 1/12,
+ * s_e = 1.25, Pr = 0.7, rho_ratio = 1.5, R_cv = R_lambda = 1, no gravity,
+ * beta = 0, T_ref = T_fluid_init = 1, adiabatic walls on four sides,
+ * mode 0, zeta = 2, eps_p = 0.01, eps_w = 0.005, FP32, 1024 particles.
+ * Returns VLB_EINVAL if p is NULL. */
+vlb_status vlb_params_default(vlb_params* p);
+
+/* Allocate a lattice of p->nx * p->ny cells on the current CUDA device and
+ * its particle arrays.  *out receives the handle (NULL on failure).  Errors:
+ * VLB_EINVAL for inconsistent parameters (tau_f <= 1/2, ratios <= 0, bad
+ * sizes, unsupported precision), VLB_ENOMEM, VLB_ECUDA. */
+vlb_status vlb_create(const vlb_params* p, vlb_handle** out);
+
+/* Queue all further work of h on cuda_stream (a cudaStream_t; NULL selects
+ * the legacy default stream).  Pending work on the previous stream is
+ * synchronised first. */
+vlb_status vlb_set_stream(vlb_handle* h, void* cuda_stream);
+
+/* Append n disks (Sec. 2.3) before the first step.  xy[2n] centres, radius[n]
+ * (>= 1 lu), T0[n] initial temperatures; k_ratio[n] per-particle
+ * lambda_s/lambda_f, uv[2n] and omega[n] initial velocities may be NULL
+ * (defaults: k_ratio_default, 0, 0).  Host arrays, copied.  Errors:
+ * VLB_ESTATE after the first step, VLB_EINVAL if a disk leaves the domain,
+ * overlaps another or crosses a periodic boundary, VLB_EOVERFLOW beyond
+ * max_particles. */
+vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const double* radius,
+                             const double* T0, const double* k_ratio, const double* uv,
+                             const double* omega);
+
+/* Advance nsteps >= 0 time steps (asynchronous).  The first call builds the
+ * initial state (f at rest, corrected by f_s^0; g at equilibrium with the
+ * volume-weighted initial temperature).  Returns a device-side failure of
+ * earlier steps if one has been recorded. */
+vlb_status vlb_step(vlb_handle* h, int32_t nsteps);
+
+/* Block until the handle's queued work is done; returns the first recorded
+ * device-side failure, else VLB_OK. */
+vlb_status vlb_synchronize(vlb_handle* h);
+
+/* Number of completed time steps in *n (after the queued work finishes). */
+vlb_status vlb_get_step(vlb_handle* h, int64_t* n);
+
+/* Copy macroscopic fields of the current time level into caller-owned host
+ * arrays of nx*ny doubles (row-major, y slow): rho, u_x, u_y, T (Eqs. 9, 25)
+ * and the solid fraction f_s.  Only arrays whose VLB_FIELD_* bit is set in
+ * mask are written; the others may be NULL. */
+vlb_status vlb_get_fields(vlb_handle* h, uint32_t mask, double* rho, double* ux, double* uy,
+                          double* T, double* fs);
+
+/* Copy the state of the first n particles (n <= count): centres xy[2n],
+ * orientation theta[n], velocity uv[2n], angular velocity omega[n], and the
+ * total force force[2n] and torque torque[n] (F_c, T_c of Eq. 26) that
+ * produced the current velocities.  Any pointer may be NULL. */
+vlb_status vlb_get_particle_state(vlb_handle* h, int32_t n, double* xy, double* theta, double* uv,
+                                  double* omega, double* force, double* torque);
+
+/* Number of particles in *n. */
+vlb_status vlb_get_particle_count(vlb_handle* h, int32_t* n);
+
+/* FP64 audits of the stored post-collision state: total mass sum_x sum_i f_i,
+ * total internal energy sum_x eps of the current level, and sum_x sum_i g_i.
+ * Any pointer may be NULL.  Sets VLB_EUNSTABLE if a population is NaN. */
+vlb_status vlb_get_audit(vlb_handle* h, double* total_mass, double* total_eps, double* total_g);
+
+/* Solid-fraction ownership of the current level (Sec. 2; integer part exact):
+ * count[nx*ny] owners per cell; owner[4*nx*ny] particle ids in ascending
+ * order, -1 padded; flag[4*nx*ny] 1 = interface, 2 = solid, 0 padded;
+ * fsp[4*nx*ny] per-owner fractions.  Arrays may be NULL. */
+vlb_status vlb_get_solid_fraction(vlb_handle* h, uint8_t* count, int32_t* owner, uint8_t* flag,
+                                  double* fsp);
+
+/* Contact pair list of the current level: pairs (i, j), i < j, with
+ * |X_i - X_j| < R_i + R_j + zeta, in ascending (i, j) order, written as
+ * pairs[2k], pairs[2k+1] for k < min(*npairs, capacity).  *npairs receives
+ * the total number of pairs. */
+vlb_status vlb_get_contact_pairs(vlb_handle* h, int32_t capacity, int32_t* pairs, int32_t* npairs);
+
+/* Measurement hooks.  Between begin and end, each step records CUDA events
+ * around its lattice kernel on the handle's stream.  end() returns the summed
+ * lattice-kernel time in ms, the number of timed launches, and the number of
+ * kernel launches each step issues. */
+vlb_status vlb_profile_begin(vlb_handle* h, int32_t max_steps);
+vlb_status vlb_profile_end(vlb_handle* h, double* lattice_ms, int32_t* lattice_launches,
+                           int32_t* launches_per_step);
+
+/* Description of the last failure on h (or of a failed vlb_create when h is
+ * NULL).  The string stays valid until the next call on the same handle. */
+const char* vlb_last_error(const vlb_handle* h);
+
+/* Free every resource of h (NULL is ignored). */
+void vlb_destroy(vlb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLB_H */

@@ -1,0 +1,623 @@
+// C ABI of the library (include/vlb.h): handle life cycle, device memory,
+// the order of the kernels within a time step, and the copies to the host.
+//
+// One time step n -> n+1 on the handle's stream:
+//   particle_advance   F_c^n from the partials of level n, contacts at X^n,
+//                      forward Euler to X^{n+1}, U^{n+1}, tile range of X^{n+1}
+//   memset, particle_bin, particle_pairs   tile lists and contact partners at X^{n+1}
+//   lattice (STEP)     fused pull / correction / thermal / collision pass that
+//                      writes level n+1 and the partials of level n+1
+// The first step is preceded by the initial state (lattice INIT mode).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vlb.h"
+#include "vlb_common.cuh"
+#include "vlb_kernels.h"
+
+using namespace vlb;
+
+struct vlb_handle {
+  vlb_params p{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int nx = 0, ny = 0, pitch = 0, ntx = 0, nty = 0;
+  long long plane = 0;
+  size_t esize = 0;          // bytes per stored population / arithmetic value
+  void* pop[2] = {nullptr, nullptr};
+  void* spl[2] = {nullptr, nullptr};
+  void* macro = nullptr;
+  int cur = 0;
+  bool initialized = false;
+  bool macros_valid = false;
+  long long step = 0;
+  // particles
+  int np = 0, cap = 0, kt = 0;
+  std::vector<double> hx, hy, hr, hT0, hk, hux, huy, hom;
+  ParticleArrays P{};
+  TileLists TL{};
+  void* pbase = nullptr;
+  // device error word and its pinned host copy (refreshed in stream order)
+  unsigned* err_host = nullptr;
+  unsigned* err_dev = nullptr;
+  double* audit_scratch = nullptr;
+  double* audit_out = nullptr;
+  int audit_blocks = 0;
+  LatticeConst<float> K32{};
+  LatticeConst<double> K64{};
+  ParticleConst PC{};
+  // profiling
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0, ev_cap = 0;
+};
+
+static thread_local std::string g_create_error;
+
+static vlb_status fail(vlb_handle* h, vlb_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+static vlb_status cuda_fail(vlb_handle* h, cudaError_t e, const char* where) {
+  return fail(h, VLB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                         \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+// Queue a copy of the device error word into pinned host memory.
+static cudaError_t pull_flags(vlb_handle* h) {
+  return cudaMemcpyAsync(h->err_host, h->err_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+}
+
+static vlb_status device_flags(vlb_handle* h) {
+  const unsigned e = *(volatile unsigned*)h->err_host;
+  if (e == 0) return VLB_OK;
+  std::string m = "device reported:";
+  if (e & ERR_TILE_OVERFLOW) m += " tile list overflow;";
+  if (e & ERR_OWNER_OVERFLOW) m += " more than 4 owners in a cell;";
+  if (e & ERR_NBR_OVERFLOW) m += " contact partner overflow;";
+  if (e & ERR_PARTIAL_OVERFLOW) m += " partial slot overflow;";
+  if (e & ERR_OUT_OF_DOMAIN) m += " particle out of the domain;";
+  if (e & ERR_TOO_FAST) m += " particle faster than 0.5 lu/step;";
+  if (e & ERR_NAN) m += " NaN population;";
+  const bool unstable = e & (ERR_OUT_OF_DOMAIN | ERR_TOO_FAST | ERR_NAN);
+  return fail(h, unstable ? VLB_EUNSTABLE : VLB_EOVERFLOW, m);
+}
+
+extern "C" {
+
+size_t vlb_params_size(void) { return sizeof(vlb_params); }
+
+vlb_status vlb_params_default(vlb_params* p) {
+  if (!p) return VLB_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->abi_version = VLB_ABI_VERSION;
+  p->nx = 64;
+  p->ny = 64;
+  p->precision = VLB_FP32;
+  p->max_particles = 1024;
+  p->tau_f = 0.8;
+  p->lambda_q_flow = 1.0 / 12.0;
+  p->s_e = 1.25;
+  p->prandtl = 0.7;
+  p->rho_ratio = 1.5;
+  p->cv_ratio = 1.0;
+  p->k_ratio_default = 1.0;
+  p->T_ref = 1.0;
+  p->T_fluid_init = 1.0;
+  p->contact_range = 2.0;
+  p->contact_eps_p = 0.01;
+  p->contact_eps_w = 0.005;
+  return VLB_OK;
+}
+
+const char* vlb_last_error(const vlb_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"
+
+template <class C>
+static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
+  const vlb_params& p = h->p;
+  K.nx = h->nx; K.ny = h->ny; K.pitch = h->pitch; K.ntx = h->ntx; K.nty = h->nty;
+  K.plane = h->plane;
+  K.per_x = p.periodic[0]; K.per_y = p.periodic[1];
+  for (int w = 0; w < 4; ++w) {
+    K.wall_dirichlet[w] = p.thermal_wall[w] == VLB_WALL_DIRICHLET;
+    K.wall_T[w] = C(p.wall_T[w]);
+  }
+  K.kt = h->kt;
+  K.np = h->np;
+  // Eq. 5 with the rules of Sec. 3
+  const double sp = 1.0 / p.tau_f;
+  const double sq = 1.0 / (0.5 + p.lambda_q_flow / (p.tau_f - 0.5));
+  K.s_e = C(p.s_e); K.s_eps = C(p.s_e); K.s_j = C(1); K.s_q = C(sq); K.s_p = C(sp);
+  // Eqs. 11, 22 with rho_f = c_vf = 1; lambda_f = nu / Pr
+  const double cvf = 1.0, cvs = p.cv_ratio;
+  const double cref = 2.0 * cvf * cvs / (cvf + cvs);
+  const double nu = (p.tau_f - 0.5) / 3.0;
+  K.cv_f = C(cvf); K.cv_s = C(cvs); K.cref = C(cref); K.lam_f = C(nu / p.prandtl);
+  K.rates_mode = C(p.thermal_rates_mode);
+  K.bx = C(-p.beta * p.gravity[0]); K.by = C(-p.beta * p.gravity[1]);
+  K.T_ref = C(p.T_ref); K.T_fluid = C(p.T_fluid_init);
+  const double Tf = p.T_fluid_init;
+  K.g_off[0] = C(Tf * (cvf - 5.0 / 9.0 * cref));
+  for (int i = 1; i < 9; ++i) K.g_off[i] = C((i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0) * cref * Tf);
+}
+
+extern "C" {
+
+static void free_all(vlb_handle* h) {
+  for (int b = 0; b < 2; ++b) {
+    if (h->pop[b]) cudaFree(h->pop[b]);
+    if (h->spl[b]) cudaFree(h->spl[b]);
+  }
+  if (h->macro) cudaFree(h->macro);
+  if (h->pbase) cudaFree(h->pbase);
+  if (h->TL.count) cudaFree(h->TL.count);
+  if (h->TL.ids) cudaFree(h->TL.ids);
+  if (h->P.partial) cudaFree(h->P.partial);
+  if (h->audit_scratch) cudaFree(h->audit_scratch);
+  if (h->err_host) cudaFreeHost(h->err_host);
+  if (h->err_dev) cudaFree(h->err_dev);
+  for (auto& e : h->ev) cudaEventDestroy(e);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
+  if (!out) return fail(nullptr, VLB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!pp) return fail(nullptr, VLB_EINVAL, "params is NULL");
+  const vlb_params& p = *pp;
+  if (p.abi_version != VLB_ABI_VERSION) return fail(nullptr, VLB_EINVAL, "abi_version mismatch");
+  if (p.nx < 2 || p.ny < 2 || p.nx > (1 << 16) || p.ny > (1 << 16))
+    return fail(nullptr, VLB_EINVAL, "nx, ny must be in [2, 65536]");
+  if (!(p.tau_f > 0.5)) return fail(nullptr, VLB_EINVAL, "tau_f must exceed 1/2");
+  if (!(p.lambda_q_flow > 0.0) || !(p.s_e > 0.0 && p.s_e < 2.0) || !(p.prandtl > 0.0))
+    return fail(nullptr, VLB_EINVAL, "lambda_q_flow, s_e or prandtl out of range");
+  if (!(p.rho_ratio > 0.0) || !(p.cv_ratio > 0.0) || !(p.k_ratio_default > 0.0))
+    return fail(nullptr, VLB_EINVAL, "rho_ratio, cv_ratio, k_ratio_default must be positive");
+  if (!(p.contact_range > 0.0) || !(p.contact_eps_p > 0.0) || !(p.contact_eps_w > 0.0))
+    return fail(nullptr, VLB_EINVAL, "contact parameters must be positive");
+  if (p.precision != VLB_FP32 && p.precision != VLB_FP64)
+    return fail(nullptr, VLB_EINVAL, "precision not supported by this build (FP32, FP64)");
+  if (p.max_particles < 0 || p.max_particles > (1 << 24)) return fail(nullptr, VLB_EINVAL, "max_particles");
+  if (p.thermal_rates_mode != 0 && p.thermal_rates_mode != 1)
+    return fail(nullptr, VLB_EINVAL, "thermal_rates_mode must be 0 or 1");
+  for (int k = 0; k < 2; ++k)
+    if (p.periodic[k] != 0 && p.periodic[k] != 1) return fail(nullptr, VLB_EINVAL, "periodic must be 0/1");
+  for (int w = 0; w < 4; ++w)
+    if (p.thermal_wall[w] != 0 && p.thermal_wall[w] != 1) return fail(nullptr, VLB_EINVAL, "thermal_wall");
+
+  vlb_handle* h = new (std::nothrow) vlb_handle();
+  if (!h) return fail(nullptr, VLB_ENOMEM, "host allocation");
+  h->p = p;
+  h->nx = p.nx;
+  h->ny = p.ny;
+  h->esize = p.precision == VLB_FP64 ? 8 : 4;
+  const int align = 128 / (int)h->esize;
+  h->pitch = (p.nx + align - 1) / align * align;
+  h->plane = (long long)h->pitch * p.ny;
+  h->ntx = (p.nx + TILE_X - 1) / TILE_X;
+  h->nty = (p.ny + TILE_Y - 1) / TILE_Y;
+  h->cap = p.max_particles;
+  auto bail = [&](cudaError_t e, const char* where) {
+    g_create_error = std::string(where) + ": " + cudaGetErrorString(e);
+    free_all(h);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? VLB_ENOMEM : VLB_ECUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
+  h->own_stream = true;
+  const size_t popbytes = (size_t)18 * h->plane * h->esize;
+  for (int b = 0; b < 2; ++b) {
+    if ((e = cudaMalloc(&h->pop[b], popbytes)) != cudaSuccess) return bail(e, "populations");
+    if ((e = cudaMalloc(&h->spl[b], (size_t)h->plane * h->esize)) != cudaSuccess) return bail(e, "S plane");
+    cudaMemsetAsync(h->spl[b], 0, (size_t)h->plane * h->esize, h->stream);
+  }
+  if ((e = cudaMalloc(&h->macro, (size_t)7 * h->plane * h->esize)) != cudaSuccess) return bail(e, "macros");
+  const long long ntiles = (long long)h->ntx * h->nty;
+  if ((e = cudaMalloc(&h->TL.count, ntiles * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
+  if ((e = cudaMalloc(&h->TL.ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
+  cudaMemsetAsync(h->TL.count, 0, ntiles * sizeof(int), h->stream);
+  // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints per particle
+  const size_t capn = (size_t)std::max(h->cap, 1);
+  const size_t pbytes = capn * (15 * sizeof(double) + sizeof(int4) + (NBR_CAP + 1) * sizeof(int));
+  if ((e = cudaMalloc(&h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
+  {
+    char* b = static_cast<char*>(h->pbase);
+    double** d[15] = {&h->P.x, &h->P.y, &h->P.theta, &h->P.ux, &h->P.uy, &h->P.om, &h->P.ux_prev,
+                      &h->P.uy_prev, &h->P.om_prev, &h->P.fcx, &h->P.fcy, &h->P.tc, &h->P.r,
+                      &h->P.lam_s, &h->P.T0};
+    for (int k = 0; k < 15; ++k) { *d[k] = reinterpret_cast<double*>(b); b += capn * sizeof(double); }
+    h->P.prange = reinterpret_cast<int4*>(b); b += capn * sizeof(int4);
+    h->P.nbr_count = reinterpret_cast<int*>(b); b += capn * sizeof(int);
+    h->P.nbr = reinterpret_cast<int*>(b);
+  }
+  cudaMemsetAsync(h->pbase, 0, pbytes, h->stream);
+  h->audit_blocks = 608;  // 4 x 152 SMs
+  if ((e = cudaMalloc(&h->audit_scratch, (3 * h->audit_blocks + 3) * sizeof(double))) != cudaSuccess)
+    return bail(e, "audit");
+  h->audit_out = h->audit_scratch + 3 * h->audit_blocks;
+  if ((e = cudaHostAlloc(&h->err_host, sizeof(unsigned), cudaHostAllocDefault)) != cudaSuccess)
+    return bail(e, "error word");
+  *h->err_host = 0;
+  if ((e = cudaMalloc(&h->err_dev, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
+  cudaMemsetAsync(h->err_dev, 0, sizeof(unsigned), h->stream);
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(e, "create sync");
+  *out = h;
+  return VLB_OK;
+}
+
+vlb_status vlb_set_stream(vlb_handle* h, void* s) {
+  if (!h) return VLB_EINVAL;
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  h->own_stream = false;
+  h->stream = static_cast<cudaStream_t>(s);
+  return VLB_OK;
+}
+
+vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const double* radius,
+                             const double* T0, const double* k_ratio, const double* uv, const double* omega) {
+  if (!h) return VLB_EINVAL;
+  if (h->initialized) return fail(h, VLB_ESTATE, "particles must be added before the first step");
+  if (n < 0 || (n > 0 && (!xy || !radius || !T0))) return fail(h, VLB_EINVAL, "bad particle arrays");
+  if (h->np + n > h->cap) return fail(h, VLB_EOVERFLOW, "max_particles exceeded");
+  const vlb_params& p = h->p;
+  for (int k = 0; k < n; ++k) {
+    const double X = xy[2 * k], Y = xy[2 * k + 1], R = radius[k];
+    if (!(R >= 1.0) || !std::isfinite(X) || !std::isfinite(Y)) return fail(h, VLB_EINVAL, "radius < 1 or bad centre");
+    const bool inx = p.periodic[0] ? (X - R - 1.0 >= 0.0 && X + R + 1.0 <= p.nx) : (X - R >= 0.0 && X + R <= p.nx);
+    const bool iny = p.periodic[1] ? (Y - R - 1.0 >= 0.0 && Y + R + 1.0 <= p.ny) : (Y - R >= 0.0 && Y + R <= p.ny);
+    if (!inx || !iny) return fail(h, VLB_EINVAL, "particle outside the domain or across a periodic boundary");
+    if (k_ratio && !(k_ratio[k] > 0.0)) return fail(h, VLB_EINVAL, "k_ratio must be positive");
+  }
+  // overlap test against existing and new disks
+  std::vector<double> X(h->hx), Y(h->hy), Rr(h->hr);
+  for (int k = 0; k < n; ++k) { X.push_back(xy[2 * k]); Y.push_back(xy[2 * k + 1]); Rr.push_back(radius[k]); }
+  std::vector<int> order(X.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return X[a] < X[b]; });
+  double rmax = 0.0;
+  for (double r : Rr) rmax = std::max(rmax, r);
+  for (size_t a = 0; a < order.size(); ++a)
+    for (size_t b = a + 1; b < order.size(); ++b) {
+      const int i = order[a], j = order[b];
+      if (X[j] - X[i] > 2.0 * rmax) break;
+      if ((size_t)i < h->hx.size() && (size_t)j < h->hx.size()) continue;
+      const double dx = X[i] - X[j], dy = Y[i] - Y[j];
+      if (dx * dx + dy * dy < (Rr[i] + Rr[j]) * (Rr[i] + Rr[j])) return fail(h, VLB_EINVAL, "particles overlap");
+    }
+  for (int k = 0; k < n; ++k) {
+    h->hx.push_back(xy[2 * k]);
+    h->hy.push_back(xy[2 * k + 1]);
+    h->hr.push_back(radius[k]);
+    h->hT0.push_back(T0[k]);
+    h->hk.push_back(k_ratio ? k_ratio[k] : p.k_ratio_default);
+    h->hux.push_back(uv ? uv[2 * k] : 0.0);
+    h->huy.push_back(uv ? uv[2 * k + 1] : 0.0);
+    h->hom.push_back(omega ? omega[k] : 0.0);
+  }
+  h->np += n;
+  return VLB_OK;
+}
+
+static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_buf) {
+  StepBuffers B;
+  B.src = h->pop[src_buf];
+  B.dst = h->pop[dst_buf];
+  B.s_src = h->spl[src_buf];
+  B.s_dst = h->spl[dst_buf];
+  B.macro = h->macro;
+  B.err = h->err_dev;
+  cudaError_t e = h->p.precision == VLB_FP64 ? launch_lattice_f64(mode, h->K64, B, h->P, h->TL, h->stream)
+                                             : launch_lattice_f32(mode, h->K32, B, h->P, h->TL, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lattice kernel");
+  return VLB_OK;
+}
+
+static vlb_status build_lists(vlb_handle* h) {
+  const long long ntiles = (long long)h->ntx * h->nty;
+  CK(h, cudaMemsetAsync(h->TL.count, 0, ntiles * sizeof(int), h->stream));
+  CK(h, launch_particle_bin(h->PC, h->P, h->TL, h->err_dev, h->stream));
+  CK(h, launch_particle_pairs(h->PC, h->P, h->TL, h->err_dev, h->stream));
+  return VLB_OK;
+}
+
+static vlb_status initialize(vlb_handle* h) {
+  const vlb_params& p = h->p;
+  const int n = h->np;
+  // partial slots: the largest tile range a disk can cover
+  double rmax = 0.0;
+  for (double r : h->hr) rmax = std::max(rmax, r);
+  const double margin = 0.5 * p.contact_range + 2.0;
+  const int span = (int)std::ceil(2.0 * (rmax + margin)) + 2;
+  h->kt = std::max(1, ((span + TILE_X - 1) / TILE_X + 1) * ((span + TILE_Y - 1) / TILE_Y + 1));
+  if (n > 0) {
+    CK(h, cudaMalloc(&h->P.partial, (size_t)n * h->kt * 3 * sizeof(double)));
+    CK(h, cudaMemsetAsync(h->P.partial, 0, (size_t)n * h->kt * 3 * sizeof(double), h->stream));
+    std::vector<double> lam(n);
+    const double lam_f = (p.tau_f - 0.5) / 3.0 / p.prandtl;
+    for (int k = 0; k < n; ++k) lam[k] = h->hk[k] * lam_f;
+    const size_t b = n * sizeof(double);
+    CK(h, cudaMemcpyAsync(h->P.x, h->hx.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.y, h->hy.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.r, h->hr.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.T0, h->hT0.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.lam_s, lam.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.ux, h->hux.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.uy, h->huy.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.om, h->hom.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.ux_prev, h->hux.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.uy_prev, h->huy.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.om_prev, h->hom.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));  // host vectors may be reused below
+  }
+  fill_const(h, h->K32);
+  fill_const(h, h->K64);
+  ParticleConst& c = h->PC;
+  c.np = n; c.nx = h->nx; c.ny = h->ny; c.per_x = p.periodic[0]; c.per_y = p.periodic[1];
+  c.ntx = h->ntx; c.nty = h->nty; c.kt = h->kt;
+  c.rho_ratio = p.rho_ratio; c.gx = p.gravity[0]; c.gy = p.gravity[1];
+  c.zeta = p.contact_range; c.eps_p = p.contact_eps_p; c.eps_w = p.contact_eps_w;
+  c.contact_scale = std::fabs(p.rho_ratio - 1.0) * std::hypot(p.gravity[0], p.gravity[1]) * M_PI;
+  c.margin = margin;
+  CK(h, launch_particle_range(c, h->P, h->err_dev, h->stream));
+  vlb_status s = build_lists(h);
+  if (s != VLB_OK) return s;
+  h->cur = 0;
+  s = launch_lattice(h, MODE_INIT, 0, 0);
+  if (s != VLB_OK) return s;
+  h->initialized = true;
+  h->macros_valid = true;
+  h->step = 0;
+  return VLB_OK;
+}
+
+vlb_status vlb_step(vlb_handle* h, int32_t nsteps) {
+  if (!h) return VLB_EINVAL;
+  if (nsteps < 0) return fail(h, VLB_EINVAL, "nsteps < 0");
+  vlb_status s = device_flags(h);
+  if (s != VLB_OK) return s;
+  if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
+  for (int k = 0; k < nsteps; ++k) {
+    CK(h, launch_particle_advance(h->PC, h->P, h->err_dev, h->stream));
+    if ((s = build_lists(h)) != VLB_OK) return s;
+    const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
+    if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
+    if ((s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur)) != VLB_OK) return s;
+    if (rec) {
+      CK(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+      h->ev_used += 2;
+    }
+    h->cur = 1 - h->cur;
+    ++h->step;
+    h->macros_valid = false;
+  }
+  CK(h, pull_flags(h));
+  return VLB_OK;
+}
+
+vlb_status vlb_synchronize(vlb_handle* h) {
+  if (!h) return VLB_EINVAL;
+  CK(h, pull_flags(h));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return device_flags(h);
+}
+
+vlb_status vlb_get_step(vlb_handle* h, int64_t* n) {
+  if (!h || !n) return VLB_EINVAL;
+  *n = h->step;
+  return VLB_OK;
+}
+
+static vlb_status ensure_ready(vlb_handle* h) {
+  vlb_status s;
+  if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
+  if (!h->macros_valid) {
+    // re-run the pre-collision part of the last step from the previous buffer
+    if ((s = launch_lattice(h, MODE_MACROS, 1 - h->cur, h->cur)) != VLB_OK) return s;
+    h->macros_valid = true;
+  }
+  CK(h, pull_flags(h));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return device_flags(h);
+}
+
+vlb_status vlb_get_fields(vlb_handle* h, uint32_t mask, double* rho, double* ux, double* uy, double* T,
+                          double* fs) {
+  if (!h) return VLB_EINVAL;
+  double* outs[5] = {rho, ux, uy, T, fs};
+  for (int k = 0; k < 5; ++k)
+    if ((mask & (1u << k)) && !outs[k]) return fail(h, VLB_EINVAL, "NULL field array for a selected field");
+  vlb_status s = ensure_ready(h);
+  if (s != VLB_OK) return s;
+  const size_t ncell = (size_t)h->nx * h->ny;
+  std::vector<char> tmp(ncell * h->esize);
+  for (int k = 0; k < 5; ++k) {
+    if (!(mask & (1u << k))) continue;
+    const char* src = static_cast<const char*>(h->macro) + (size_t)k * h->plane * h->esize;
+    CK(h, cudaMemcpy2D(tmp.data(), h->nx * h->esize, src, h->pitch * h->esize, h->nx * h->esize, h->ny,
+                       cudaMemcpyDeviceToHost));
+    if (h->esize == 8) std::memcpy(outs[k], tmp.data(), ncell * 8);
+    else {
+      const float* f = reinterpret_cast<const float*>(tmp.data());
+      for (size_t c = 0; c < ncell; ++c) outs[k][c] = f[c];
+    }
+  }
+  return VLB_OK;
+}
+
+vlb_status vlb_get_particle_count(vlb_handle* h, int32_t* n) {
+  if (!h || !n) return VLB_EINVAL;
+  *n = h->np;
+  return VLB_OK;
+}
+
+vlb_status vlb_get_particle_state(vlb_handle* h, int32_t n, double* xy, double* theta, double* uv,
+                                  double* omega, double* force, double* torque) {
+  if (!h) return VLB_EINVAL;
+  if (n < 0 || n > h->np) return fail(h, VLB_EINVAL, "n exceeds the particle count");
+  if (n == 0) return VLB_OK;
+  if (!h->initialized) {
+    // state before the first step is the uploaded one
+    for (int k = 0; k < n; ++k) {
+      if (xy) { xy[2 * k] = h->hx[k]; xy[2 * k + 1] = h->hy[k]; }
+      if (theta) theta[k] = 0.0;
+      if (uv) { uv[2 * k] = h->hux[k]; uv[2 * k + 1] = h->huy[k]; }
+      if (omega) omega[k] = h->hom[k];
+      if (force) { force[2 * k] = 0.0; force[2 * k + 1] = 0.0; }
+      if (torque) torque[k] = 0.0;
+    }
+    return VLB_OK;
+  }
+  CK(h, pull_flags(h));
+  CK(h, cudaStreamSynchronize(h->stream));
+  std::vector<double> a(n), b(n);
+  auto get = [&](const double* d, std::vector<double>& v) {
+    return cudaMemcpy(v.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost);
+  };
+  if (xy) {
+    CK(h, get(h->P.x, a)); CK(h, get(h->P.y, b));
+    for (int k = 0; k < n; ++k) { xy[2 * k] = a[k]; xy[2 * k + 1] = b[k]; }
+  }
+  if (uv) {
+    CK(h, get(h->P.ux, a)); CK(h, get(h->P.uy, b));
+    for (int k = 0; k < n; ++k) { uv[2 * k] = a[k]; uv[2 * k + 1] = b[k]; }
+  }
+  if (force) {
+    CK(h, get(h->P.fcx, a)); CK(h, get(h->P.fcy, b));
+    for (int k = 0; k < n; ++k) { force[2 * k] = a[k]; force[2 * k + 1] = b[k]; }
+  }
+  if (theta) CK(h, cudaMemcpy(theta, h->P.theta, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (omega) CK(h, cudaMemcpy(omega, h->P.om, n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (torque) CK(h, cudaMemcpy(torque, h->P.tc, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return device_flags(h);
+}
+
+vlb_status vlb_get_audit(vlb_handle* h, double* total_mass, double* total_eps, double* total_g) {
+  if (!h) return VLB_EINVAL;
+  vlb_status s = ensure_ready(h);
+  if (s != VLB_OK) return s;
+  cudaError_t e = h->p.precision == VLB_FP64
+                      ? launch_audit_f64(h->K64, h->pop[h->cur], h->macro, h->audit_scratch, h->audit_blocks,
+                                         h->audit_out, h->err_dev, h->stream)
+                      : launch_audit_f32(h->K32, h->pop[h->cur], h->macro, h->audit_scratch, h->audit_blocks,
+                                         h->audit_out, h->err_dev, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "audit");
+  double o[3];
+  CK(h, cudaMemcpyAsync(o, h->audit_out, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, pull_flags(h));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (total_mass) *total_mass = o[0];
+  if (total_eps) *total_eps = o[1];
+  if (total_g) *total_g = o[2];
+  return device_flags(h);
+}
+
+vlb_status vlb_get_solid_fraction(vlb_handle* h, uint8_t* count, int32_t* owner, uint8_t* flag, double* fsp) {
+  if (!h) return VLB_EINVAL;
+  vlb_status s = ensure_ready(h);
+  if (s != VLB_OK) return s;
+  const size_t ncell = (size_t)h->nx * h->ny;
+  unsigned char *dc = nullptr, *df = nullptr;
+  int* dow = nullptr;
+  double* dfs = nullptr;
+  cudaError_t e = cudaMalloc(&dc, ncell);
+  if (e == cudaSuccess) e = cudaMalloc(&df, 4 * ncell);
+  if (e == cudaSuccess) e = cudaMalloc(&dow, 4 * ncell * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&dfs, 4 * ncell * sizeof(double));
+  if (e == cudaSuccess)
+    e = h->p.precision == VLB_FP64
+            ? launch_raster_dump_f64(h->K64, h->P, h->TL, dc, dow, df, dfs, h->err_dev, h->stream)
+            : launch_raster_dump_f32(h->K32, h->P, h->TL, dc, dow, df, dfs, h->err_dev, h->stream);
+  if (e == cudaSuccess) e = pull_flags(h);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && count) e = cudaMemcpy(count, dc, ncell, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && flag) e = cudaMemcpy(flag, df, 4 * ncell, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && owner) e = cudaMemcpy(owner, dow, 4 * ncell * sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && fsp) e = cudaMemcpy(fsp, dfs, 4 * ncell * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dc);
+  cudaFree(df);
+  cudaFree(dow);
+  cudaFree(dfs);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solid fraction dump");
+  return device_flags(h);
+}
+
+vlb_status vlb_get_contact_pairs(vlb_handle* h, int32_t capacity, int32_t* pairs, int32_t* npairs) {
+  if (!h || !npairs || capacity < 0 || (capacity > 0 && !pairs)) return VLB_EINVAL;
+  vlb_status s = ensure_ready(h);
+  if (s != VLB_OK) return s;
+  const int n = h->np;
+  std::vector<int> cnt(n), nbr((size_t)n * NBR_CAP);
+  if (n > 0) {
+    CK(h, cudaMemcpy(cnt.data(), h->P.nbr_count, n * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(nbr.data(), h->P.nbr, (size_t)n * NBR_CAP * sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  int total = 0;
+  for (int i = 0; i < n; ++i)
+    for (int a = 0; a < std::min(cnt[i], NBR_CAP); ++a) {
+      const int j = nbr[(size_t)i * NBR_CAP + a];
+      if (j <= i) continue;
+      if (total < capacity) { pairs[2 * total] = i; pairs[2 * total + 1] = j; }
+      ++total;
+    }
+  *npairs = total;
+  return VLB_OK;
+}
+
+vlb_status vlb_profile_begin(vlb_handle* h, int32_t max_steps) {
+  if (!h || max_steps < 0) return VLB_EINVAL;
+  CK(h, cudaStreamSynchronize(h->stream));
+  const int need = 2 * max_steps;
+  while ((int)h->ev.size() < need) {
+    cudaEvent_t e;
+    CK(h, cudaEventCreate(&e));
+    h->ev.push_back(e);
+  }
+  h->ev_cap = need;
+  h->ev_used = 0;
+  h->prof = true;
+  return VLB_OK;
+}
+
+vlb_status vlb_profile_end(vlb_handle* h, double* lattice_ms, int32_t* lattice_launches,
+                           int32_t* launches_per_step) {
+  if (!h) return VLB_EINVAL;
+  CK(h, cudaStreamSynchronize(h->stream));
+  double tot = 0.0;
+  for (int k = 0; k + 1 < h->ev_used; k += 2) {
+    float ms = 0.f;
+    CK(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+    tot += ms;
+  }
+  if (lattice_ms) *lattice_ms = tot;
+  if (lattice_launches) *lattice_launches = h->ev_used / 2;
+  // particle_advance, particle_bin, particle_pairs, lattice (the memset is not a kernel)
+  if (launches_per_step) *launches_per_step = h->np > 0 ? 4 : 1;
+  h->prof = false;
+  h->ev_used = 0;
+  return VLB_OK;
+}
+
+void vlb_destroy(vlb_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Shared definitions of the sm_103a kernels: lattice constants, the data
+// layout in HBM, kernel argument blocks and device-side error bits.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vlb {
+
+// ---------------------------------------------------------------------------
+// D2Q9 velocity set of Eq. 2 (c = 1) and opposite directions.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ex(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+  return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp");
+
+// D2Q9 weights: f^eq(1, 0) = M^-1 m^eq(1, 0) of Eqs. 4 and 6.
+template <class C>
+__host__ __device__ constexpr C wgt(int i) {
+  return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// Tiles of the lattice kernel: one CTA of 32 x 8 threads per 32 x 8 cells.
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 8;
+constexpr int TILE_CAP = 32;   // particles listed per tile
+constexpr int MAX_OWNERS = 4;  // particles owning one cell
+constexpr int NBR_CAP = 16;    // contact partners per particle
+constexpr int QBITS = 20;      // fixed-point grid of the integer cell tests
+
+// Device error bits (mapped host word).
+enum : unsigned {
+  ERR_TILE_OVERFLOW = 1u,
+  ERR_OWNER_OVERFLOW = 2u,
+  ERR_NBR_OVERFLOW = 4u,
+  ERR_PARTIAL_OVERFLOW = 8u,
+  ERR_OUT_OF_DOMAIN = 16u,
+  ERR_TOO_FAST = 32u,
+  ERR_NAN = 64u,
+};
+
+// Kernel modes of the lattice kernel.
+enum : int { MODE_INIT = 0, MODE_STEP = 1, MODE_MACROS = 2 };
+
+// ---------------------------------------------------------------------------
+// Particle arrays (SoA, FP64) -- Sec. 2.3.
+// ---------------------------------------------------------------------------
+struct ParticleArrays {
+  double *x, *y, *theta, *ux, *uy, *om;
+  double *ux_prev, *uy_prev, *om_prev;
+  double *fcx, *fcy, *tc;  // F_c, T_c of the last update
+  double *r, *lam_s, *T0;  // radius, lambda_s, initial temperature
+  int4* prange;            // tile range (tx0, ty0, ntx, nty) at the current level
+  double* partial;         // [n][kt][3] MES partial sums per tile of the range
+  int* nbr_count;          // contact partners per particle
+  int* nbr;                // [n][NBR_CAP], ascending ids
+};
+
+struct TileLists {
+  int* count;  // [ntiles]
+  int* ids;    // [ntiles][TILE_CAP], unordered
+};
+
+// Problem constants in the arithmetic type C of the lattice kernel.
+template <class C>
+struct LatticeConst {
+  int nx, ny, pitch, ntx, nty;
+  long long plane;         // elements per population plane
+  int per_x, per_y;        // periodic axes
+  int wall_dirichlet[4];   // x-, x+, y-, y+
+  int kt;                  // partial slots per particle
+  int np;
+  // flow rates (Eq. 5)
+  C s_e, s_eps, s_j, s_q, s_p;
+  // thermal (Eqs. 11, 18-22)
+  C cv_f, cv_s, cref, lam_f, rates_mode;
+  C bx, by, T_ref, T_fluid;  // buoyancy b = -rho_f beta g
+  C wall_T[4];
+  C g_off[9];              // storage offset of g (rest equilibrium at T_fluid)
+};
+
+struct StepBuffers {
+  void* src;     // populations at level n (18 planes of the storage type)
+  void* dst;     // populations at level n+1
+  void* s_src;   // S = 2 f_s + df_s/dt at level n (one plane, arithmetic type)
+  void* s_dst;
+  void* macro;   // rho, ux, uy, T, fs planes (arithmetic type); may be null
+  unsigned* err;
+};
+
+}  // namespace vlb

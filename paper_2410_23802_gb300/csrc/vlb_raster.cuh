@@ -1,0 +1,151 @@
+// Solid fraction of a disk in one lattice cell (Sec. 2: f_s is the volume
+// fraction of solid in the cell, fixed by the particle position).
+//
+// Classification (integer, identical on every device): a cell is SOLID when
+// its four corners lie in the closed disk and FLUID when its nearest point is
+// at distance >= R, tested on centres and radii rounded to a 2^-20 grid.
+// INTERFACE cells get the exact area of disk ∩ cell, computed in cell-local
+// coordinates as a polygon (cell corners inside the disk plus the circle's
+// crossings of the cell edges) plus the circular segments between each chord
+// and its arc -- all quantities are O(1), so FP32 keeps ~1e-7 absolute error.
+#pragma once
+
+#include "vlb_common.cuh"
+
+namespace vlb {
+
+enum : int { CELL_FLUID = 0, CELL_INTERFACE = 1, CELL_SOLID = 2 };
+
+// One particle as seen from one tile (shared memory).  Coordinates are
+// relative to the tile's lower-left corner.
+template <class C>
+struct PartTile {
+  long long xq, yq, rq2;  // fixed-point centre and R^2 (2^-20 grid)
+  C xh, xl, yh, yl;       // centre as an unevaluated sum hi + lo
+  C r, far2, near2;       // radius, quick-reject bounds on the centre distance^2
+  C ux, uy, om;           // rigid-body motion (Eq. 27)
+  C lam_s, T0;
+  int id, k;              // particle id; index of this tile in its partial slots
+};
+
+// Integer classification of cell (il, jl) of the tile against one disk.
+template <class C>
+__device__ __forceinline__ int cell_class_exact(int il, int jl, const PartTile<C>& p) {
+  const long long Q = 1ll << QBITS;
+  const long long cx0 = (long long)il * Q - p.xq, cx1 = cx0 + Q;
+  const long long cy0 = (long long)jl * Q - p.yq, cy1 = cy0 + Q;
+  const long long fx = cx0 * cx0 > cx1 * cx1 ? cx0 * cx0 : cx1 * cx1;
+  const long long fy = cy0 * cy0 > cy1 * cy1 ? cy0 * cy0 : cy1 * cy1;
+  if (fx + fy <= p.rq2) return CELL_SOLID;
+  const long long ax0 = cx0 < 0 ? -cx0 : cx0, ax1 = cx1 < 0 ? -cx1 : cx1;
+  const long long ay0 = cy0 < 0 ? -cy0 : cy0, ay1 = cy1 < 0 ? -cy1 : cy1;
+  const long long nx = (cx0 <= 0 && cx1 >= 0) ? 0 : (ax0 < ax1 ? ax0 : ax1);
+  const long long ny = (cy0 <= 0 && cy1 >= 0) ? 0 : (ay0 < ay1 ? ay0 : ay1);
+  if (nx * nx + ny * ny >= p.rq2) return CELL_FLUID;
+  return CELL_INTERFACE;
+}
+
+// Area of the circular segment cut off by a chord of length L (L <= 2R):
+// R^2 (asin z - z sqrt(1 - z^2)), z = L / (2R).
+__device__ __forceinline__ double segment_area(double L, double R) {
+  const double z = L / (2.0 * R);
+  return R * R * (asin(z) - z * sqrt(fmax(1.0 - z * z, 0.0)));
+}
+__device__ __forceinline__ float segment_area(float L, float R) {
+  const float z = L / (2.0f * R);
+  if (z < 0.25f) {
+    // Taylor series of asin z - z sqrt(1 - z^2):
+    // 2/3 z^3 + 1/5 z^5 + 3/28 z^7 + 5/72 z^9 + 35/704 z^11 + O(z^13)
+    const float z2 = z * z;
+    float s = 35.0f / 704.0f;
+    s = s * z2 + 5.0f / 72.0f;
+    s = s * z2 + 3.0f / 28.0f;
+    s = s * z2 + 0.2f;
+    s = s * z2 + 2.0f / 3.0f;
+    return R * R * s * z2 * z;
+  }
+  return R * R * (asinf(z) - z * sqrtf(fmaxf(1.0f - z * z, 0.0f)));
+}
+
+// Exact area of disk((cx, cy), R) ∩ [0,1]^2 (cell-local coordinates).
+template <class C>
+__device__ C disk_unit_cell_area(C cx, C cy, C R) {
+  const C R2 = R * R;
+  C px[12], py[12];
+  int ty[12];  // 0 corner, 1 entry into the disk, 2 exit from the disk
+  int n = 0;
+  // square corners counter-clockwise; edge k runs from corner k to corner k+1
+  const C qx[4] = {C(0), C(1), C(1), C(0)};
+  const C qy[4] = {C(0), C(0), C(1), C(1)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const C ax = qx[k], ay = qy[k];
+    const C dx = ax - cx, dy = ay - cy;
+    if (dx * dx + dy * dy < R2) {
+      px[n] = ax; py[n] = ay; ty[n] = 0; ++n;
+    }
+    // crossings of the open edge, in walking order
+    const bool horiz = (k == 0 || k == 2);
+    const C fixed = horiz ? ay : ax;           // y of a horizontal edge, x of a vertical one
+    const C c_fix = horiz ? cy : cx;
+    const C c_run = horiz ? cx : cy;
+    const C d = fixed - c_fix;
+    const C ad = d < C(0) ? -d : d;
+    const C h = (R - ad) * (R + ad);
+    if (h > C(0)) {
+      const C s = sqrt(h);
+      const C lo = c_run - s, hi = c_run + s;  // entry/exit when walking upward
+      const bool up = (k == 0 || k == 1);      // edges 0, 1 run in +x / +y
+      const C first = up ? lo : hi, second = up ? hi : lo;
+      if (first > C(0) && first < C(1)) {
+        px[n] = horiz ? first : fixed; py[n] = horiz ? fixed : first; ty[n] = 1; ++n;
+      }
+      if (second > C(0) && second < C(1)) {
+        px[n] = horiz ? second : fixed; py[n] = horiz ? fixed : second; ty[n] = 2; ++n;
+      }
+    }
+  }
+  if (n == 0) return C(0);
+  C twice = C(0);
+  for (int a = 0; a < n; ++a) {
+    const int b = (a + 1 == n) ? 0 : a + 1;
+    twice += px[a] * py[b] - px[b] * py[a];
+  }
+  C seg = C(0);
+  for (int a = 0; a < n; ++a) {
+    if (ty[a] != 2) continue;
+    // the next crossing after an exit is the entry that closes the arc
+    for (int s = 1; s < n; ++s) {
+      const int b = (a + s) % n;
+      if (ty[b] == 0) continue;
+      if (ty[b] == 1) {
+        const C lx = px[b] - px[a], ly = py[b] - py[a];
+        const C L = sqrt(lx * lx + ly * ly);
+        seg += segment_area(L < C(2) * R ? L : C(2) * R, R);
+      }
+      break;
+    }
+  }
+  C area = C(0.5) * twice + seg;
+  return area < C(0) ? C(0) : (area > C(1) ? C(1) : area);
+}
+
+// Class and solid fraction of tile cell (il, jl) for one particle.
+template <class C>
+__device__ __forceinline__ int cell_fraction(int il, int jl, const PartTile<C>& p, C& fsp) {
+  // centre distance from the cell centre (hi/lo sums keep FP32 exact enough)
+  const C dx = ((C(il) + C(0.5)) - p.xh) - p.xl;
+  const C dy = ((C(jl) + C(0.5)) - p.yh) - p.yl;
+  const C d2 = dx * dx + dy * dy;
+  if (d2 >= p.far2) { fsp = C(0); return CELL_FLUID; }   // nearest point > R + 0.04
+  if (d2 <= p.near2) { fsp = C(1); return CELL_SOLID; }  // farthest corner < R - 0.04
+  const int cls = cell_class_exact(il, jl, p);
+  if (cls == CELL_SOLID) { fsp = C(1); return cls; }
+  if (cls == CELL_FLUID) { fsp = C(0); return cls; }
+  const C cx = (p.xh - C(il)) + p.xl;  // disk centre in cell-local coordinates
+  const C cy = (p.yh - C(jl)) + p.yl;
+  fsp = disk_unit_cell_area(cx, cy, p.r);
+  return cls;
+}
+
+}  // namespace vlb

@@ -1,0 +1,271 @@
+"""Thin Python binding of the C ABI in ``include/vlb.h`` (ctypes).
+
+The functions carry the C names and only marshal arguments: every step of the
+method runs in the CUDA kernels of ``libvlb.so``.  There is no CPU fallback;
+importing this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvlb.so")
+
+VLB_ABI_VERSION = 1
+VLB_OK, VLB_EINVAL, VLB_ENOMEM, VLB_ECUDA, VLB_ESTATE, VLB_EUNSTABLE, VLB_EOVERFLOW, VLB_ETIMEOUT = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+VLB_FP64, VLB_FP32, VLB_FP16_STORE, VLB_BF16_STORE = 0, 1, 2, 3
+VLB_WALL_ADIABATIC, VLB_WALL_DIRICHLET = 0, 1
+VLB_FIELD_RHO, VLB_FIELD_UX, VLB_FIELD_UY, VLB_FIELD_T, VLB_FIELD_FS = 1, 2, 4, 8, 16
+VLB_FIELD_ALL = 31
+
+STATUS_NAMES = {0: "VLB_OK", -1: "VLB_EINVAL", -2: "VLB_ENOMEM", -3: "VLB_ECUDA", -4: "VLB_ESTATE",
+                -5: "VLB_EUNSTABLE", -6: "VLB_EOVERFLOW", -7: "VLB_ETIMEOUT"}
+
+
+class vlb_params(ctypes.Structure):
+    """Mirror of ``vlb_params`` in include/vlb.h (same order and types)."""
+    _fields_ = [
+        ("abi_version", ctypes.c_uint32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("periodic", ctypes.c_int32 * 2),
+        ("thermal_wall", ctypes.c_int32 * 4),
+        ("thermal_rates_mode", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("max_particles", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("tau_f", ctypes.c_double),
+        ("lambda_q_flow", ctypes.c_double),
+        ("s_e", ctypes.c_double),
+        ("prandtl", ctypes.c_double),
+        ("rho_ratio", ctypes.c_double),
+        ("cv_ratio", ctypes.c_double),
+        ("k_ratio_default", ctypes.c_double),
+        ("gravity", ctypes.c_double * 2),
+        ("beta", ctypes.c_double),
+        ("T_ref", ctypes.c_double),
+        ("T_fluid_init", ctypes.c_double),
+        ("wall_T", ctypes.c_double * 4),
+        ("contact_range", ctypes.c_double),
+        ("contact_eps_p", ctypes.c_double),
+        ("contact_eps_w", ctypes.c_double),
+    ]
+
+
+class VlbError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2410_23802_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    d = P(ctypes.c_double)
+    h = ctypes.c_void_p
+    sig = {
+        "vlb_params_size": (ctypes.c_size_t, []),
+        "vlb_params_default": (ctypes.c_int, [P(vlb_params)]),
+        "vlb_create": (ctypes.c_int, [P(vlb_params), P(ctypes.c_void_p)]),
+        "vlb_set_stream": (ctypes.c_int, [h, ctypes.c_void_p]),
+        "vlb_add_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
+        "vlb_step": (ctypes.c_int, [h, ctypes.c_int32]),
+        "vlb_synchronize": (ctypes.c_int, [h]),
+        "vlb_get_step": (ctypes.c_int, [h, P(ctypes.c_int64)]),
+        "vlb_get_fields": (ctypes.c_int, [h, ctypes.c_uint32, d, d, d, d, d]),
+        "vlb_get_particle_state": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
+        "vlb_get_particle_count": (ctypes.c_int, [h, P(ctypes.c_int32)]),
+        "vlb_get_audit": (ctypes.c_int, [h, d, d, d]),
+        "vlb_get_solid_fraction": (ctypes.c_int, [h, P(ctypes.c_uint8), P(ctypes.c_int32),
+                                                  P(ctypes.c_uint8), d]),
+        "vlb_get_contact_pairs": (ctypes.c_int, [h, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]),
+        "vlb_profile_begin": (ctypes.c_int, [h, ctypes.c_int32]),
+        "vlb_profile_end": (ctypes.c_int, [h, d, P(ctypes.c_int32), P(ctypes.c_int32)]),
+        "vlb_last_error": (ctypes.c_char_p, [h]),
+        "vlb_destroy": (None, [h]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if lib.vlb_params_size() != ctypes.sizeof(vlb_params):
+        raise ImportError("vlb_params layout differs between include/vlb.h and the binding")
+    return lib
+
+
+_lib = _load()
+
+
+def _ptr(a, ctype=ctypes.c_double):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _check(status: int, h=None):
+    if status != VLB_OK:
+        msg = _lib.vlb_last_error(h)
+        raise VlbError(status, msg.decode() if msg else "")
+
+
+def vlb_params_default(**overrides) -> vlb_params:
+    p = vlb_params()
+    _check(_lib.vlb_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if k in ("periodic", "thermal_wall", "wall_T", "gravity"):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def vlb_create(params: vlb_params):
+    h = ctypes.c_void_p()
+    _check(_lib.vlb_create(ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def vlb_set_stream(h, stream_ptr: int):
+    _check(_lib.vlb_set_stream(h, ctypes.c_void_p(stream_ptr)), h)
+
+
+def vlb_add_particles(h, xy, radius, T0, k_ratio=None, uv=None, omega=None):
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+    radius = np.ascontiguousarray(radius, dtype=np.float64)
+    T0 = np.ascontiguousarray(T0, dtype=np.float64)
+    n = radius.shape[0]
+    conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)  # noqa: E731
+    k_ratio, uv, omega = conv(k_ratio), conv(uv), conv(omega)
+    _check(_lib.vlb_add_particles(h, n, _ptr(xy), _ptr(radius), _ptr(T0), _ptr(k_ratio), _ptr(uv), _ptr(omega)), h)
+
+
+def vlb_step(h, nsteps: int = 1):
+    _check(_lib.vlb_step(h, int(nsteps)), h)
+
+
+def vlb_synchronize(h):
+    _check(_lib.vlb_synchronize(h), h)
+
+
+def vlb_get_step(h) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.vlb_get_step(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def vlb_get_fields(h, nx: int, ny: int, mask: int = VLB_FIELD_ALL, out: dict | None = None) -> dict:
+    names = ["rho", "ux", "uy", "T", "fs"]
+    res = {} if out is None else out
+    arrs = []
+    for k, nm in enumerate(names):
+        if mask & (1 << k):
+            a = res.get(nm)
+            if a is None or a.shape != (ny, nx):
+                a = np.empty((ny, nx), dtype=np.float64)
+            res[nm] = a
+            arrs.append(a)
+        else:
+            arrs.append(None)
+    _check(_lib.vlb_get_fields(h, mask, *[_ptr(a) for a in arrs]), h)
+    return res
+
+
+def vlb_get_particle_count(h) -> int:
+    n = ctypes.c_int32()
+    _check(_lib.vlb_get_particle_count(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def vlb_get_particle_state(h, n: int | None = None) -> dict:
+    n = vlb_get_particle_count(h) if n is None else n
+    xy, uv, force = np.empty((n, 2)), np.empty((n, 2)), np.empty((n, 2))
+    theta, omega, torque = np.empty(n), np.empty(n), np.empty(n)
+    _check(_lib.vlb_get_particle_state(h, n, _ptr(xy), _ptr(theta), _ptr(uv), _ptr(omega), _ptr(force),
+                                       _ptr(torque)), h)
+    return {"x": xy[:, 0].copy(), "y": xy[:, 1].copy(), "theta": theta, "ux": uv[:, 0].copy(),
+            "uy": uv[:, 1].copy(), "omega": omega, "fx": force[:, 0].copy(), "fy": force[:, 1].copy(),
+            "torque": torque}
+
+
+def vlb_get_audit(h):
+    m, e, g = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.vlb_get_audit(h, ctypes.byref(m), ctypes.byref(e), ctypes.byref(g)), h)
+    return m.value, e.value, g.value
+
+
+def vlb_get_solid_fraction(h, nx: int, ny: int):
+    count = np.empty((ny, nx), dtype=np.uint8)
+    owner = np.empty((ny, nx, 4), dtype=np.int32)
+    flag = np.empty((ny, nx, 4), dtype=np.uint8)
+    fsp = np.empty((ny, nx, 4), dtype=np.float64)
+    _check(_lib.vlb_get_solid_fraction(h, _ptr(count, ctypes.c_uint8), _ptr(owner, ctypes.c_int32),
+                                       _ptr(flag, ctypes.c_uint8), _ptr(fsp)), h)
+    return count, owner, flag, fsp
+
+
+def vlb_get_contact_pairs(h) -> np.ndarray:
+    n = ctypes.c_int32()
+    _check(_lib.vlb_get_contact_pairs(h, 0, None, ctypes.byref(n)), h)
+    buf = np.empty(2 * max(n.value, 1), dtype=np.int32)
+    _check(_lib.vlb_get_contact_pairs(h, n.value, _ptr(buf, ctypes.c_int32), ctypes.byref(n)), h)
+    return buf[: 2 * n.value].reshape(-1, 2)
+
+
+def vlb_profile_begin(h, max_steps: int):
+    _check(_lib.vlb_profile_begin(h, int(max_steps)), h)
+
+
+def vlb_profile_end(h):
+    ms, nl, lps = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.vlb_profile_end(h, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(lps)), h)
+    return ms.value, nl.value, lps.value
+
+
+def vlb_last_error(h=None) -> str:
+    msg = _lib.vlb_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def vlb_destroy(h):
+    if h is not None and h.value:
+        _lib.vlb_destroy(h)
+        h.value = None
+
+
+class Lattice:
+    """Owning wrapper of one handle (closes it on exit)."""
+
+    def __init__(self, params: vlb_params):
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        self.h = vlb_create(params)
+
+    def add_particles(self, *a, **k):
+        vlb_add_particles(self.h, *a, **k)
+
+    def step(self, n: int = 1):
+        vlb_step(self.h, n)
+
+    def fields(self, mask: int = VLB_FIELD_ALL) -> dict:
+        return vlb_get_fields(self.h, self.nx, self.ny, mask)
+
+    def particles(self) -> dict:
+        return vlb_get_particle_state(self.h)
+
+    def audit(self):
+        return vlb_get_audit(self.h)
+
+    def close(self):
+        vlb_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,129 @@
+"""Seeded synthetic cases shaped like the paper's experiments.
+
+This module holds no arithmetic of the method: it draws particle placements
+with a counter-based generator (SplitMix64) and lists the problem parameters
+of each case.  Both the CUDA path and the test oracle take their inputs from
+here.
+
+Cases
+-----
+channel   one cold disk settling in a closed channel (Sec. 3.4 proportions):
+          100 x 400 cells, D = 20 at (50, 300), tau_f = 0.8, rho_s/rho_f = 1.5,
+          g = 1e-5, fluid T = 1, particle T = 0, R_lambda = 2, R_cv = 1.5,
+          Pr = 0.7, beta = 12.5 (Gr = 100 on D), adiabatic no-slip walls.
+cavity    cold disks in a square cavity (Sec. 3.5): side L, N disks of D = 16
+          at seeded non-overlapping uniform centres in the upper 60 % with
+          gaps >= 2 lu between disks and from the walls, rho_s/rho_f = 1.2,
+          bottom wall T = 1, top wall T = 0, adiabatic sides, fluid T = 1,
+          particles T = 0, R_lambda = 5 (or per-particle log-uniform in
+          [0.1, 10]), R_cv = 2, Pr = 0.71, tau_f = 0.8, sigma_0 = sigma_e =
+          sigma_eps = 1 (Sec. 3.5), g = 1e-5, beta from Gr = 100 on D.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+MASK64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """Counter-based generator of Steele, Lea & Flood (2014)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+
+@dataclasses.dataclass
+class Case:
+    """Problem parameters (names of include/vlb.h) and the particle arrays."""
+    name: str
+    params: dict
+    x: list
+    y: list
+    radius: list
+    T0: list
+    k_ratio: list | None = None
+
+    @property
+    def cells(self) -> int:
+        return self.params["nx"] * self.params["ny"]
+
+
+def place_disks(nx: int, ny: int, n: int, diameter: float, seed: int, y_min_frac: float = 0.4,
+                gap: float = 2.0, max_tries: int = 2_000_000):
+    """Rejection sampling of n disk centres, uniform in
+    [R + gap, nx - R - gap] x [max(y_min_frac * ny, 0) + R + gap, ny - R - gap],
+    keeping centre distances >= diameter + gap."""
+    rng = SplitMix64(seed)
+    R = 0.5 * diameter
+    x_lo, x_hi = R + gap, nx - R - gap
+    y_lo, y_hi = y_min_frac * ny + R + gap, ny - R - gap
+    cell = diameter + gap
+    grid: dict = {}
+    xs, ys = [], []
+    tries = 0
+    while len(xs) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError(f"could not place {n} disks (placed {len(xs)})")
+        x = rng.uniform(x_lo, x_hi)
+        y = rng.uniform(y_lo, y_hi)
+        gx, gy = int(x // cell), int(y // cell)
+        ok = True
+        for a in (gx - 1, gx, gx + 1):
+            for b in (gy - 1, gy, gy + 1):
+                for k in grid.get((a, b), ()):
+                    if (xs[k] - x) ** 2 + (ys[k] - y) ** 2 < cell * cell:
+                        ok = False
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if ok:
+            grid.setdefault((gx, gy), []).append(len(xs))
+            xs.append(x)
+            ys.append(y)
+    return xs, ys
+
+
+def gr_beta(gr: float, nu: float, g: float, dT: float, D: float) -> float:
+    """Volume expansivity giving a Grashof number gr on the diameter (Eq. 32)."""
+    return gr * nu * nu / (g * dT * D ** 3)
+
+
+def channel(precision: str = "fp64") -> Case:
+    nu = (0.8 - 0.5) / 3.0
+    params = dict(nx=100, ny=400, tau_f=0.8, prandtl=0.7, rho_ratio=1.5, cv_ratio=1.5, k_ratio_default=2.0,
+                  gravity=(0.0, -1e-5), beta=gr_beta(100.0, nu, 1e-5, 1.0, 20.0), T_ref=1.0, T_fluid_init=1.0,
+                  thermal_wall=(0, 0, 0, 0), wall_T=(0.0, 0.0, 0.0, 0.0), thermal_rates_mode=0,
+                  precision=precision)
+    return Case("channel 100x400, 1 disk D=20", params, [50.0], [300.0], [10.0], [0.0])
+
+
+def cavity(side: int = 2048, n: int = 2048, diameter: float = 16.0, seed: int = 20241031,
+           precision: str = "fp32", k_log_uniform: bool = False) -> Case:
+    nu = (0.8 - 0.5) / 3.0
+    g = 1e-5
+    xs, ys = place_disks(side, side, n, diameter, seed)
+    params = dict(nx=side, ny=side, tau_f=0.8, prandtl=0.71, rho_ratio=1.2, cv_ratio=2.0, k_ratio_default=5.0,
+                  gravity=(0.0, -g), beta=gr_beta(100.0, nu, g, 1.0, diameter), T_ref=1.0, T_fluid_init=1.0,
+                  thermal_wall=(0, 0, 1, 1), wall_T=(0.0, 0.0, 1.0, 0.0), thermal_rates_mode=1,
+                  precision=precision)
+    k = None
+    if k_log_uniform:
+        rng = SplitMix64(seed ^ 0x5DEECE66D)
+        k = [10.0 ** rng.uniform(-1.0, 1.0) for _ in range(n)]
+    return Case(f"cavity {side}x{side}, {n} disks D={diameter:g}", params, xs, ys, [0.5 * diameter] * n,
+                [0.0] * n, k)

@@ -1,0 +1,34 @@
+"""Test-only glue: the same seeded case fed to the CUDA path and the oracle."""
+import numpy as np
+
+PREC = {"fp64": 0, "fp32": 1}
+
+
+def gpu_lattice(case, precision=None, max_particles=None, **over):
+    from paper_2410_23802_gb300 import vlb as V
+    prm = dict(case.params)
+    prm.update(over)
+    prec = PREC[precision or prm.pop("precision", "fp32")]
+    prm.pop("precision", None)
+    n = len(case.x)
+    p = V.vlb_params_default(precision=prec, max_particles=max_particles or max(n, 1), **prm)
+    lat = V.Lattice(p)
+    if n:
+        xy = np.column_stack([case.x, case.y])
+        lat.add_particles(xy, case.radius, case.T0, k_ratio=case.k_ratio)
+    return lat
+
+
+def oracle_sim(case, **over):
+    from oracle import vlbref as O
+    prm = {k: v for k, v in case.params.items() if k != "precision"}
+    prm.update(over)
+    if "periodic" in prm:
+        prm["periodic"] = tuple(bool(v) for v in prm["periodic"])
+    return O.Simulation(O.Params(**prm), case.x, case.y, case.radius, case.T0, k_ratio=case.k_ratio)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
