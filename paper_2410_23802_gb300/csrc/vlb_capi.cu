@@ -231,18 +231,21 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   if ((e = cudaMalloc(&h->TL.count, ntiles * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
   if ((e = cudaMalloc(&h->TL.ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
   cudaMemsetAsync(h->TL.count, 0, ntiles * sizeof(int), h->stream);
-  // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints per particle
+  // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints per particle; every
+  // sub-array starts on a 256-byte boundary (int4 loads need 16-byte alignment)
   const size_t capn = (size_t)std::max(h->cap, 1);
-  const size_t pbytes = capn * (15 * sizeof(double) + sizeof(int4) + (NBR_CAP + 1) * sizeof(int));
+  auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t pbytes = 15 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) +
+                        a256(capn * sizeof(int)) + a256(capn * NBR_CAP * sizeof(int));
   if ((e = cudaMalloc(&h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
   {
     char* b = static_cast<char*>(h->pbase);
     double** d[15] = {&h->P.x, &h->P.y, &h->P.theta, &h->P.ux, &h->P.uy, &h->P.om, &h->P.ux_prev,
                       &h->P.uy_prev, &h->P.om_prev, &h->P.fcx, &h->P.fcy, &h->P.tc, &h->P.r,
                       &h->P.lam_s, &h->P.T0};
-    for (int k = 0; k < 15; ++k) { *d[k] = reinterpret_cast<double*>(b); b += capn * sizeof(double); }
-    h->P.prange = reinterpret_cast<int4*>(b); b += capn * sizeof(int4);
-    h->P.nbr_count = reinterpret_cast<int*>(b); b += capn * sizeof(int);
+    for (int k = 0; k < 15; ++k) { *d[k] = reinterpret_cast<double*>(b); b += a256(capn * sizeof(double)); }
+    h->P.prange = reinterpret_cast<int4*>(b); b += a256(capn * sizeof(int4));
+    h->P.nbr_count = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.nbr = reinterpret_cast<int*>(b);
   }
   cudaMemsetAsync(h->pbase, 0, pbytes, h->stream);

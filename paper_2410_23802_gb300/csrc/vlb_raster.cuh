@@ -5,14 +5,19 @@
 // its four corners lie in the closed disk and FLUID when its nearest point is
 // at distance >= R, tested on centres and radii rounded to a 2^-20 grid.
 // INTERFACE cells get the exact area of disk ∩ cell, computed in cell-local
-// coordinates as a polygon (cell corners inside the disk plus the circle's
-// crossings of the cell edges) plus the circular segments between each chord
-// and its arc -- all quantities are O(1), so FP32 keeps ~1e-7 absolute error.
+// coordinates as a polygon (the parts of the cell edges inside the disk) plus
+// the circular segments between each chord and its arc -- all quantities are
+// O(1), so FP32 keeps ~1e-7 absolute error.
 #pragma once
+
+#include <math.h>
 
 #include "vlb_common.cuh"
 
 namespace vlb {
+
+__host__ __device__ __forceinline__ float vsqrt(float v) { return sqrtf(v); }
+__host__ __device__ __forceinline__ double vsqrt(double v) { return sqrt(v); }
 
 enum : int { CELL_FLUID = 0, CELL_INTERFACE = 1, CELL_SOLID = 2 };
 
@@ -30,7 +35,7 @@ struct PartTile {
 
 // Integer classification of cell (il, jl) of the tile against one disk.
 template <class C>
-__device__ __forceinline__ int cell_class_exact(int il, int jl, const PartTile<C>& p) {
+__host__ __device__ __forceinline__ int cell_class_exact(int il, int jl, const PartTile<C>& p) {
   const long long Q = 1ll << QBITS;
   const long long cx0 = (long long)il * Q - p.xq, cx1 = cx0 + Q;
   const long long cy0 = (long long)jl * Q - p.yq, cy1 = cy0 + Q;
@@ -47,11 +52,11 @@ __device__ __forceinline__ int cell_class_exact(int il, int jl, const PartTile<C
 
 // Area of the circular segment cut off by a chord of length L (L <= 2R):
 // R^2 (asin z - z sqrt(1 - z^2)), z = L / (2R).
-__device__ __forceinline__ double segment_area(double L, double R) {
+__host__ __device__ __forceinline__ double segment_area(double L, double R) {
   const double z = L / (2.0 * R);
   return R * R * (asin(z) - z * sqrt(fmax(1.0 - z * z, 0.0)));
 }
-__device__ __forceinline__ float segment_area(float L, float R) {
+__host__ __device__ __forceinline__ float segment_area(float L, float R) {
   const float z = L / (2.0f * R);
   if (z < 0.25f) {
     // Taylor series of asin z - z sqrt(1 - z^2):
@@ -67,72 +72,58 @@ __device__ __forceinline__ float segment_area(float L, float R) {
   return R * R * (asinf(z) - z * sqrtf(fmaxf(1.0f - z * z, 0.0f)));
 }
 
-// Exact area of disk((cx, cy), R) ∩ [0,1]^2 (cell-local coordinates).
+// Exact area of disk((cx, cy), R) ∩ [0,1]^2 (cell-local coordinates), R >= 1.
+//
+// Walking the square's boundary counter-clockwise, each edge meets the closed
+// disk in one interval (possibly empty), found from that edge's own line.  The
+// region's boundary is those intervals joined, between one interval's end and
+// the next interval's start, by arcs of the circle; so the area is the polygon
+// of the interval end points plus, for every such link, the circular segment
+// on its chord.  No entry/exit decision is taken: when rounding puts a circle
+// point on one or the other side of a corner, the link's chord is just tiny
+// and so is its segment.
 template <class C>
-__device__ C disk_unit_cell_area(C cx, C cy, C R) {
-  const C R2 = R * R;
-  C px[12], py[12];
-  int ty[12];  // 0 corner, 1 entry into the disk, 2 exit from the disk
+__host__ __device__ C disk_unit_cell_area(C cx, C cy, C R) {
+  C px[8], py[8];
   int n = 0;
-  // square corners counter-clockwise; edge k runs from corner k to corner k+1
-  const C qx[4] = {C(0), C(1), C(1), C(0)};
-  const C qy[4] = {C(0), C(0), C(1), C(1)};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const C ax = qx[k], ay = qy[k];
-    const C dx = ax - cx, dy = ay - cy;
-    if (dx * dx + dy * dy < R2) {
-      px[n] = ax; py[n] = ay; ty[n] = 0; ++n;
-    }
-    // crossings of the open edge, in walking order
+    // edge 0: y = 0, x 0 -> 1; edge 1: x = 1, y 0 -> 1; edge 2: y = 1, x 1 -> 0;
+    // edge 3: x = 0, y 1 -> 0
     const bool horiz = (k == 0 || k == 2);
-    const C fixed = horiz ? ay : ax;           // y of a horizontal edge, x of a vertical one
-    const C c_fix = horiz ? cy : cx;
-    const C c_run = horiz ? cx : cy;
-    const C d = fixed - c_fix;
+    const C fixed = (k == 1 || k == 2) ? C(1) : C(0);
+    const C d = fixed - (horiz ? cy : cx);
     const C ad = d < C(0) ? -d : d;
-    const C h = (R - ad) * (R + ad);
-    if (h > C(0)) {
-      const C s = sqrt(h);
-      const C lo = c_run - s, hi = c_run + s;  // entry/exit when walking upward
-      const bool up = (k == 0 || k == 1);      // edges 0, 1 run in +x / +y
-      const C first = up ? lo : hi, second = up ? hi : lo;
-      if (first > C(0) && first < C(1)) {
-        px[n] = horiz ? first : fixed; py[n] = horiz ? fixed : first; ty[n] = 1; ++n;
-      }
-      if (second > C(0) && second < C(1)) {
-        px[n] = horiz ? second : fixed; py[n] = horiz ? fixed : second; ty[n] = 2; ++n;
-      }
-    }
+    if (ad >= R) continue;
+    const C s = vsqrt((R - ad) * (R + ad));
+    const C c_run = horiz ? cx : cy;
+    C lo = c_run - s, hi = c_run + s;
+    lo = lo < C(0) ? C(0) : lo;
+    hi = hi > C(1) ? C(1) : hi;
+    if (!(hi > lo)) continue;
+    const bool up = (k == 0 || k == 1);
+    const C a = up ? lo : hi, b = up ? hi : lo;  // start and end in walking order
+    px[n] = horiz ? a : fixed; py[n] = horiz ? fixed : a; ++n;
+    px[n] = horiz ? b : fixed; py[n] = horiz ? fixed : b; ++n;
   }
   if (n == 0) return C(0);
-  C twice = C(0);
+  C twice = C(0), seg = C(0);
   for (int a = 0; a < n; ++a) {
     const int b = (a + 1 == n) ? 0 : a + 1;
     twice += px[a] * py[b] - px[b] * py[a];
-  }
-  C seg = C(0);
-  for (int a = 0; a < n; ++a) {
-    if (ty[a] != 2) continue;
-    // the next crossing after an exit is the entry that closes the arc
-    for (int s = 1; s < n; ++s) {
-      const int b = (a + s) % n;
-      if (ty[b] == 0) continue;
-      if (ty[b] == 1) {
-        const C lx = px[b] - px[a], ly = py[b] - py[a];
-        const C L = sqrt(lx * lx + ly * ly);
-        seg += segment_area(L < C(2) * R ? L : C(2) * R, R);
-      }
-      break;
+    if (a & 1) {  // end of one interval -> start of the next: an arc
+      const C lx = px[b] - px[a], ly = py[b] - py[a];
+      const C L = vsqrt(lx * lx + ly * ly);
+      if (L > C(0)) seg += segment_area(L < C(2) * R ? L : C(2) * R, R);
     }
   }
-  C area = C(0.5) * twice + seg;
+  const C area = C(0.5) * twice + seg;
   return area < C(0) ? C(0) : (area > C(1) ? C(1) : area);
 }
 
 // Class and solid fraction of tile cell (il, jl) for one particle.
 template <class C>
-__device__ __forceinline__ int cell_fraction(int il, int jl, const PartTile<C>& p, C& fsp) {
+__host__ __device__ __forceinline__ int cell_fraction(int il, int jl, const PartTile<C>& p, C& fsp) {
   // centre distance from the cell centre (hi/lo sums keep FP32 exact enough)
   const C dx = ((C(il) + C(0.5)) - p.xh) - p.xl;
   const C dy = ((C(jl) + C(0.5)) - p.yh) - p.yl;
