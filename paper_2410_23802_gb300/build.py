@@ -39,9 +39,20 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 
 def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile (if needed) and return the path of libvlb.so."""
+    """Compile (if needed) and return the path of libvlb.so.
+
+    Extra preprocessor definitions (tuning constants such as
+    VLB_LATTICE_MIN_BLOCKS=4) come from the environment variable VLB_DEFINES;
+    a change of them forces a rebuild."""
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    defines = ["-D" + d for d in os.environ.get("VLB_DEFINES", "").split()]
+    stamp = os.path.join(BUILD, "defines.txt")
+    old = open(stamp).read() if os.path.exists(stamp) else ""
+    if old != " ".join(defines):
+        force = True
+        with open(stamp, "w") as fh:
+            fh.write(" ".join(defines))
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "vlb.h"))
     jobs = []
@@ -51,7 +62,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc, *ARCH, *FLAGS, "-I", os.path.join(ROOT, "include"), "-c", s, "-o", o])
+            jobs.append([nvcc, *ARCH, *FLAGS, *defines, "-I", os.path.join(ROOT, "include"), "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -2,17 +2,19 @@
 // the order of the kernels within a time step, and the copies to the host.
 //
 // One time step n -> n+1 on the handle's stream:
-//   particle_advance   F_c^n from the partials of level n, contacts at X^n,
-//                      forward Euler to X^{n+1}, U^{n+1}, tile range of X^{n+1}
-//   memset, particle_bin, particle_pairs   tile lists and contact partners at X^{n+1}
+//   particle_advance   F_c^n from the partials and contact forces of level n,
+//                      forward Euler to X^{n+1}, U^{n+1}; appends each particle
+//                      to the tile lists of X^{n+1} (list buffer b)
 //   lattice (STEP)     fused pull / correction / thermal / collision pass that
-//                      writes level n+1 and the partials of level n+1
+//                      writes level n+1, the partials and contact partners of
+//                      level n+1, and clears list buffer 1 - b for the next step
 // The first step is preceded by the initial state (lattice INIT mode).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/vlb.h"
@@ -40,7 +42,8 @@ struct vlb_handle {
   int np = 0, cap = 0, kt = 0;
   std::vector<double> hx, hy, hr, hT0, hk, hux, huy, hom;
   ParticleArrays P{};
-  TileLists TL{};
+  TileLists TL[2] = {};
+  int tl = 0;  // list buffer of the current level
   void* pbase = nullptr;
   // device error word and its pinned host copy (refreshed in stream order)
   unsigned* err_host = nullptr;
@@ -134,7 +137,7 @@ static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
   K.per_x = p.periodic[0]; K.per_y = p.periodic[1];
   for (int w = 0; w < 4; ++w) {
     K.wall_dirichlet[w] = p.thermal_wall[w] == VLB_WALL_DIRICHLET;
-    K.wall_T[w] = C(p.wall_T[w]);
+    K.wall_dT[w] = C(p.wall_T[w] - p.T_fluid_init);
   }
   K.kt = h->kt;
   K.np = h->np;
@@ -150,9 +153,14 @@ static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
   K.rates_mode = C(p.thermal_rates_mode);
   K.bx = C(-p.beta * p.gravity[0]); K.by = C(-p.beta * p.gravity[1]);
   K.T_ref = C(p.T_ref); K.T_fluid = C(p.T_fluid_init);
-  const double Tf = p.T_fluid_init;
-  K.g_off[0] = C(Tf * (cvf - 5.0 / 9.0 * cref));
-  for (int i = 1; i < 9; ++i) K.g_off[i] = C((i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0) * cref * Tf);
+  K.dT_ref = C(p.T_fluid_init - p.T_ref);
+  const double tgf = 0.5 + 3.0 * (nu / p.prandtl) / cref;
+  K.tau_gf = C(tgf);
+  K.sj_f = C(1.0 / tgf);
+  K.se_f = C(p.thermal_rates_mode == 0 ? 1.0 / (0.5 + 0.25 / (tgf - 0.5)) : 1.0);
+  K.gk_f = C(-3.0 / (cref * tgf));
+  const double dv[4] = {9.0, 36.0, 6.0, 12.0};
+  for (int k = 0; k < 4; ++k) K.rcp[k] = C(1.0 / dv[k]);
 }
 
 extern "C" {
@@ -164,8 +172,10 @@ static void free_all(vlb_handle* h) {
   }
   if (h->macro) cudaFree(h->macro);
   if (h->pbase) cudaFree(h->pbase);
-  if (h->TL.count) cudaFree(h->TL.count);
-  if (h->TL.ids) cudaFree(h->TL.ids);
+  for (int b = 0; b < 2; ++b) {
+    if (h->TL[b].count) cudaFree(h->TL[b].count);
+    if (h->TL[b].ids) cudaFree(h->TL[b].ids);
+  }
   if (h->P.partial) cudaFree(h->P.partial);
   if (h->audit_scratch) cudaFree(h->audit_scratch);
   if (h->err_host) cudaFreeHost(h->err_host);
@@ -208,6 +218,10 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   const int align = 128 / (int)h->esize;
   h->pitch = (p.nx + align - 1) / align * align;
   h->plane = (long long)h->pitch * p.ny;
+  if (h->plane >= (1ll << 31)) {
+    delete h;
+    return fail(nullptr, VLB_EINVAL, "lattice too large for 32-bit cell offsets");
+  }
   h->ntx = (p.nx + TILE_X - 1) / TILE_X;
   h->nty = (p.ny + TILE_Y - 1) / TILE_Y;
   h->cap = p.max_particles;
@@ -228,15 +242,19 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   }
   if ((e = cudaMalloc(&h->macro, (size_t)7 * h->plane * h->esize)) != cudaSuccess) return bail(e, "macros");
   const long long ntiles = (long long)h->ntx * h->nty;
-  if ((e = cudaMalloc(&h->TL.count, ntiles * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
-  if ((e = cudaMalloc(&h->TL.ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
-  cudaMemsetAsync(h->TL.count, 0, ntiles * sizeof(int), h->stream);
-  // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints per particle; every
-  // sub-array starts on a 256-byte boundary (int4 loads need 16-byte alignment)
+  for (int b = 0; b < 2; ++b) {
+    if ((e = cudaMalloc(&h->TL[b].count, ntiles * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
+    if ((e = cudaMalloc(&h->TL[b].ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
+    cudaMemsetAsync(h->TL[b].count, 0, ntiles * sizeof(int), h->stream);
+  }
+  // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints and 2 NBR_CAP
+  // doubles per particle; every sub-array starts on a 256-byte boundary (int4
+  // loads need 16-byte alignment)
   const size_t capn = (size_t)std::max(h->cap, 1);
   auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t pbytes = 15 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) +
-                        a256(capn * sizeof(int)) + a256(capn * NBR_CAP * sizeof(int));
+                        a256(capn * sizeof(int)) + a256(capn * NBR_CAP * sizeof(int)) +
+                        a256(capn * NBR_CAP * 2 * sizeof(double));
   if ((e = cudaMalloc(&h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
   {
     char* b = static_cast<char*>(h->pbase);
@@ -246,7 +264,8 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     for (int k = 0; k < 15; ++k) { *d[k] = reinterpret_cast<double*>(b); b += a256(capn * sizeof(double)); }
     h->P.prange = reinterpret_cast<int4*>(b); b += a256(capn * sizeof(int4));
     h->P.nbr_count = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
-    h->P.nbr = reinterpret_cast<int*>(b);
+    h->P.nbr = reinterpret_cast<int*>(b); b += a256(capn * NBR_CAP * sizeof(int));
+    h->P.nbr_f = reinterpret_cast<double*>(b);
   }
   cudaMemsetAsync(h->pbase, 0, pbytes, h->stream);
   h->audit_blocks = 608;  // 4 x 152 SMs
@@ -317,7 +336,9 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
   return VLB_OK;
 }
 
-static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_buf) {
+// Lattice pass with list buffer `lists`; STEP and INIT also clear the other
+// list buffer for the next particle step.
+static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_buf, int lists) {
   StepBuffers B;
   B.src = h->pop[src_buf];
   B.dst = h->pop[dst_buf];
@@ -325,17 +346,11 @@ static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_b
   B.s_dst = h->spl[dst_buf];
   B.macro = h->macro;
   B.err = h->err_dev;
-  cudaError_t e = h->p.precision == VLB_FP64 ? launch_lattice_f64(mode, h->K64, B, h->P, h->TL, h->stream)
-                                             : launch_lattice_f32(mode, h->K32, B, h->P, h->TL, h->stream);
+  TileLists TL = h->TL[lists];
+  TL.next_count = mode == MODE_MACROS ? nullptr : h->TL[1 - lists].count;
+  cudaError_t e = h->p.precision == VLB_FP64 ? launch_lattice_f64(mode, h->K64, B, h->P, TL, h->stream)
+                                             : launch_lattice_f32(mode, h->K32, B, h->P, TL, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "lattice kernel");
-  return VLB_OK;
-}
-
-static vlb_status build_lists(vlb_handle* h) {
-  const long long ntiles = (long long)h->ntx * h->nty;
-  CK(h, cudaMemsetAsync(h->TL.count, 0, ntiles * sizeof(int), h->stream));
-  CK(h, launch_particle_bin(h->PC, h->P, h->TL, h->err_dev, h->stream));
-  CK(h, launch_particle_pairs(h->PC, h->P, h->TL, h->err_dev, h->stream));
   return VLB_OK;
 }
 
@@ -377,11 +392,14 @@ static vlb_status initialize(vlb_handle* h) {
   c.zeta = p.contact_range; c.eps_p = p.contact_eps_p; c.eps_w = p.contact_eps_w;
   c.contact_scale = std::fabs(p.rho_ratio - 1.0) * std::hypot(p.gravity[0], p.gravity[1]) * M_PI;
   c.margin = margin;
+  h->K32.zeta = h->K64.zeta = p.contact_range;
+  h->K32.contact_scale = h->K64.contact_scale = c.contact_scale;
+  h->K32.eps_p = h->K64.eps_p = p.contact_eps_p;
   CK(h, launch_particle_range(c, h->P, h->err_dev, h->stream));
-  vlb_status s = build_lists(h);
-  if (s != VLB_OK) return s;
+  h->tl = 0;
+  CK(h, launch_particle_bin(c, h->P, h->TL[0], h->err_dev, h->stream));
   h->cur = 0;
-  s = launch_lattice(h, MODE_INIT, 0, 0);
+  vlb_status s = launch_lattice(h, MODE_INIT, 0, 0, 0);
   if (s != VLB_OK) return s;
   h->initialized = true;
   h->macros_valid = true;
@@ -396,11 +414,12 @@ vlb_status vlb_step(vlb_handle* h, int32_t nsteps) {
   if (s != VLB_OK) return s;
   if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
   for (int k = 0; k < nsteps; ++k) {
-    CK(h, launch_particle_advance(h->PC, h->P, h->err_dev, h->stream));
-    if ((s = build_lists(h)) != VLB_OK) return s;
+    const int nl = 1 - h->tl;
+    CK(h, launch_particle_advance(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
     const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
     if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
-    if ((s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur)) != VLB_OK) return s;
+    if ((s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur, nl)) != VLB_OK) return s;
+    h->tl = nl;
     if (rec) {
       CK(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
       h->ev_used += 2;
@@ -431,7 +450,7 @@ static vlb_status ensure_ready(vlb_handle* h) {
   if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
   if (!h->macros_valid) {
     // re-run the pre-collision part of the last step from the previous buffer
-    if ((s = launch_lattice(h, MODE_MACROS, 1 - h->cur, h->cur)) != VLB_OK) return s;
+    if ((s = launch_lattice(h, MODE_MACROS, 1 - h->cur, h->cur, h->tl)) != VLB_OK) return s;
     h->macros_valid = true;
   }
   CK(h, pull_flags(h));
@@ -544,8 +563,8 @@ vlb_status vlb_get_solid_fraction(vlb_handle* h, uint8_t* count, int32_t* owner,
   if (e == cudaSuccess) e = cudaMalloc(&dfs, 4 * ncell * sizeof(double));
   if (e == cudaSuccess)
     e = h->p.precision == VLB_FP64
-            ? launch_raster_dump_f64(h->K64, h->P, h->TL, dc, dow, df, dfs, h->err_dev, h->stream)
-            : launch_raster_dump_f32(h->K32, h->P, h->TL, dc, dow, df, dfs, h->err_dev, h->stream);
+            ? launch_raster_dump_f64(h->K64, h->P, h->TL[h->tl], dc, dow, df, dfs, h->err_dev, h->stream)
+            : launch_raster_dump_f32(h->K32, h->P, h->TL[h->tl], dc, dow, df, dfs, h->err_dev, h->stream);
   if (e == cudaSuccess) e = pull_flags(h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess && count) e = cudaMemcpy(count, dc, ncell, cudaMemcpyDeviceToHost);
@@ -570,14 +589,18 @@ vlb_status vlb_get_contact_pairs(vlb_handle* h, int32_t capacity, int32_t* pairs
     CK(h, cudaMemcpy(cnt.data(), h->P.nbr_count, n * sizeof(int), cudaMemcpyDeviceToHost));
     CK(h, cudaMemcpy(nbr.data(), h->P.nbr, (size_t)n * NBR_CAP * sizeof(int), cudaMemcpyDeviceToHost));
   }
-  int total = 0;
+  std::vector<std::pair<int, int>> pr;
   for (int i = 0; i < n; ++i)
     for (int a = 0; a < std::min(cnt[i], NBR_CAP); ++a) {
       const int j = nbr[(size_t)i * NBR_CAP + a];
-      if (j <= i) continue;
-      if (total < capacity) { pairs[2 * total] = i; pairs[2 * total + 1] = j; }
-      ++total;
+      if (j > i) pr.emplace_back(i, j);
     }
+  std::sort(pr.begin(), pr.end());
+  const int total = (int)pr.size();
+  for (int k = 0; k < std::min(total, capacity); ++k) {
+    pairs[2 * k] = pr[k].first;
+    pairs[2 * k + 1] = pr[k].second;
+  }
   *npairs = total;
   return VLB_OK;
 }
@@ -609,8 +632,8 @@ vlb_status vlb_profile_end(vlb_handle* h, double* lattice_ms, int32_t* lattice_l
   }
   if (lattice_ms) *lattice_ms = tot;
   if (lattice_launches) *lattice_launches = h->ev_used / 2;
-  // particle_advance, particle_bin, particle_pairs, lattice (the memset is not a kernel)
-  if (launches_per_step) *launches_per_step = h->np > 0 ? 4 : 1;
+  // particle_advance (with binning) and the lattice kernel
+  if (launches_per_step) *launches_per_step = h->np > 0 ? 2 : 1;
   h->prof = false;
   h->ev_used = 0;
   return VLB_OK;
@@ -624,3 +647,4 @@ void vlb_destroy(vlb_handle* h) {
 }
 
 }  // extern "C"
+

@@ -61,13 +61,25 @@ struct ParticleArrays {
   int4* prange;            // tile range (tx0, ty0, ntx, nty) at the current level
   double* partial;         // [n][kt][3] MES partial sums per tile of the range
   int* nbr_count;          // contact partners per particle
-  int* nbr;                // [n][NBR_CAP], ascending ids
+  int* nbr;                // [n][NBR_CAP], unordered (sorted where used)
+  double* nbr_f;           // [n][NBR_CAP][2] contact force on the particle from that partner
 };
 
 struct TileLists {
-  int* count;  // [ntiles]
-  int* ids;    // [ntiles][TILE_CAP], unordered
+  int* count;       // [ntiles]
+  int* ids;         // [ntiles][TILE_CAP], unordered
+  int* next_count;  // counts of the other list buffer, cleared by the lattice kernel (may be null)
 };
+
+// Contact decision d_ij^2 < (R_i + R_j + zeta)^2 in FP64 without contraction,
+// so that every device and the reference arithmetic take it identically.
+__device__ __forceinline__ bool in_contact_range(double xi, double yi, double ri, double xj, double yj,
+                                                 double rj, double zeta) {
+  const double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
+  const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+  const double thr = __dadd_rn(__dadd_rn(ri, rj), zeta);
+  return d2 < __dmul_rn(thr, thr);
+}
 
 // Problem constants in the arithmetic type C of the lattice kernel.
 template <class C>
@@ -78,13 +90,19 @@ struct LatticeConst {
   int wall_dirichlet[4];   // x-, x+, y-, y+
   int kt;                  // partial slots per particle
   int np;
+  double zeta;             // contact range
+  double contact_scale;    // |rho_r - 1| rho_f |g| pi
+  double eps_p;            // particle-particle stiffness parameter
   // flow rates (Eq. 5)
   C s_e, s_eps, s_j, s_q, s_p;
   // thermal (Eqs. 11, 18-22)
   C cv_f, cv_s, cref, lam_f, rates_mode;
-  C bx, by, T_ref, T_fluid;  // buoyancy b = -rho_f beta g
-  C wall_T[4];
-  C g_off[9];              // storage offset of g (rest equilibrium at T_fluid)
+  C bx, by, T_ref, T_fluid;  // buoyancy b = -rho_f beta g; T_f = initial fluid temperature
+  C dT_ref;                  // T_f - T_ref
+  C tau_gf, sj_f, se_f, gk_f;  // thermal rates of a fluid cell (Eqs. 18, 22, 23)
+  // rounded 1/9, 1/36, 1/6, 1/12 of M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+  C rcp[4];
+  C wall_dT[4];              // T_w - T_f per side
 };
 
 struct StepBuffers {

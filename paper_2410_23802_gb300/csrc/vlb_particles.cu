@@ -4,10 +4,10 @@
 //     of Eq. 28; the inside-fluid force and torque of Eq. 29 with backward
 //     differences; the short-range contact force; Eqs. 26 and 30 by forward
 //     Euler; the tile range of the new position.
-//   particle_bin: appends each particle to the lists of the tiles its range
-//     covers (the lattice kernel sorts each list by id).
-//   particle_pairs: contact partners found through the shared tiles, each pair
-//     accepted in its first common tile, stored in ascending id.
+//     The same thread then appends the particle to the tile lists of its new
+//     range (the lattice kernel sorts each list by id and finds the contact
+//     partners of the next level).
+//   particle_bin: the appending alone (initial state).
 #include <math.h>
 
 #include "vlb_common.cuh"
@@ -43,7 +43,19 @@ __global__ void particle_range_kernel(const ParticleConst c, const ParticleArray
   P.prange[p] = rg;
 }
 
-__global__ void particle_advance_kernel(const ParticleConst c, const ParticleArrays P, unsigned* err) {
+__device__ __forceinline__ void bin_particle(const ParticleConst& c, const TileLists& TL, int p, int4 rg,
+                                             unsigned* err) {
+  for (int b = 0; b < rg.w; ++b)
+    for (int a = 0; a < rg.z; ++a) {
+      const int t = (rg.y + b) * c.ntx + (rg.x + a);
+      const int slot = atomicAdd(&TL.count[t], 1);
+      if (slot < TILE_CAP) TL.ids[(long long)t * TILE_CAP + slot] = p;
+      else atomicOr(err, ERR_TILE_OVERFLOW);
+    }
+}
+
+__global__ void particle_advance_kernel(const ParticleConst c, const ParticleArrays P, const TileLists TL,
+                                        unsigned* err) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.np) return;
   const double X = P.x[p], Y = P.y[p], R = P.r[p];
@@ -58,19 +70,23 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
     Fm_y += part[3 * k + 1];
     Tm += part[3 * k + 2];
   }
-  // contact force: partners in ascending id, then walls x-, x+, y-, y+
+  // contact force: partner forces (computed at this level by the lattice
+  // kernel) summed in ascending partner id, then walls x-, x+, y-, y+
   double Fc_x = 0.0, Fc_y = 0.0;
   const int nn = min(P.nbr_count[p], NBR_CAP);
+  int nb[NBR_CAP];
+  double nfx[NBR_CAP], nfy[NBR_CAP];
   for (int a = 0; a < nn; ++a) {
     const int j = P.nbr[p * NBR_CAP + a];
-    const double dx = X - P.x[j], dy = Y - P.y[j];
-    const double d = sqrt(dx * dx + dy * dy);
-    const double gap = R + P.r[j] + c.zeta - d;
-    if (gap <= 0.0) continue;
-    const double Rm = fmax(R, P.r[j]);
-    const double mag = (c.contact_scale * Rm * Rm / c.eps_p) * (gap / c.zeta) * (gap / c.zeta) / d;
-    Fc_x += mag * dx;
-    Fc_y += mag * dy;
+    const double fx = P.nbr_f[2 * (p * NBR_CAP + a)], fy = P.nbr_f[2 * (p * NBR_CAP + a) + 1];
+    int k = a;
+    while (k > 0 && nb[k - 1] > j) { nb[k] = nb[k - 1]; nfx[k] = nfx[k - 1]; nfy[k] = nfy[k - 1]; --k; }
+    nb[k] = j; nfx[k] = fx; nfy[k] = fy;
+  }
+  P.nbr_count[p] = 0;  // the lattice kernel of this step lists the next partners
+  for (int a = 0; a < nn; ++a) {
+    Fc_x += nfx[a];
+    Fc_y += nfy[a];
   }
   {
     const double cw = c.contact_scale * R * R / c.eps_w;
@@ -117,62 +133,14 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   const int4 nr = tile_range(c, Xn, Yn, R);
   if (nr.z * nr.w > c.kt) atomicOr(err, ERR_PARTIAL_OVERFLOW);
   P.prange[p] = nr;
+  bin_particle(c, TL, p, nr, err);
 }
 
 __global__ void particle_bin_kernel(const ParticleConst c, const ParticleArrays P, const TileLists TL,
                                     unsigned* err) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.np) return;
-  const int4 rg = P.prange[p];
-  for (int b = 0; b < rg.w; ++b)
-    for (int a = 0; a < rg.z; ++a) {
-      const int t = (rg.y + b) * c.ntx + (rg.x + a);
-      const int slot = atomicAdd(&TL.count[t], 1);
-      if (slot < TILE_CAP) TL.ids[(long long)t * TILE_CAP + slot] = p;
-      else atomicOr(err, ERR_TILE_OVERFLOW);
-    }
-}
-
-// Contact decision d_ij^2 < (R_i + R_j + zeta)^2 in FP64 without contraction,
-// so that every device and the reference arithmetic take it identically.
-__device__ __forceinline__ bool in_contact_range(double xi, double yi, double ri, double xj, double yj,
-                                                 double rj, double zeta) {
-  const double dx = __dsub_rn(xi, xj), dy = __dsub_rn(yi, yj);
-  const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-  const double thr = __dadd_rn(__dadd_rn(ri, rj), zeta);
-  return d2 < __dmul_rn(thr, thr);
-}
-
-__global__ void particle_pairs_kernel(const ParticleConst c, const ParticleArrays P, const TileLists TL,
-                                      unsigned* err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= c.np) return;
-  const int4 ri = P.prange[i];
-  const double xi = P.x[i], yi = P.y[i], rad = P.r[i];
-  int nb[NBR_CAP];
-  int n = 0;
-  bool overflow = false;
-  for (int b = 0; b < ri.w; ++b)
-    for (int a = 0; a < ri.z; ++a) {
-      const int tx = ri.x + a, ty = ri.y + b;
-      const int t = ty * c.ntx + tx;
-      const int cnt = min(TL.count[t], TILE_CAP);
-      for (int s = 0; s < cnt; ++s) {
-        const int j = TL.ids[(long long)t * TILE_CAP + s];
-        if (j == i) continue;
-        const int4 rj = P.prange[j];
-        // accept the pair only in the first tile both ranges share
-        if (tx != max(ri.x, rj.x) || ty != max(ri.y, rj.y)) continue;
-        if (!in_contact_range(xi, yi, rad, P.x[j], P.y[j], P.r[j], c.zeta)) continue;
-        if (n == NBR_CAP) { overflow = true; continue; }
-        int k = n++;
-        while (k > 0 && nb[k - 1] > j) { nb[k] = nb[k - 1]; --k; }
-        nb[k] = j;
-      }
-    }
-  if (overflow) atomicOr(err, ERR_NBR_OVERFLOW);
-  P.nbr_count[i] = n;
-  for (int k = 0; k < n; ++k) P.nbr[i * NBR_CAP + k] = nb[k];
+  bin_particle(c, TL, p, P.prange[p], err);
 }
 
 static inline dim3 pgrid(int n) { return dim3((unsigned)((n + 127) / 128)); }
@@ -183,10 +151,10 @@ cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& 
   particle_range_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, err);
   return cudaGetLastError();
 }
-cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, unsigned* err,
-                                    cudaStream_t st) {
+cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
+                                    unsigned* err, cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
-  particle_advance_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, err);
+  particle_advance_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, TL, err);
   return cudaGetLastError();
 }
 cudaError_t launch_particle_bin(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
@@ -195,11 +163,4 @@ cudaError_t launch_particle_bin(const ParticleConst& c, const ParticleArrays& P,
   particle_bin_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, TL, err);
   return cudaGetLastError();
 }
-cudaError_t launch_particle_pairs(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
-                                  unsigned* err, cudaStream_t st) {
-  if (c.np == 0) return cudaSuccess;
-  particle_pairs_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, TL, err);
-  return cudaGetLastError();
-}
-
 }  // namespace vlb

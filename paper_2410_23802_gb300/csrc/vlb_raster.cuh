@@ -29,8 +29,10 @@ struct PartTile {
   C xh, xl, yh, yl;       // centre as an unevaluated sum hi + lo
   C r, far2, near2;       // radius, quick-reject bounds on the centre distance^2
   C ux, uy, om;           // rigid-body motion (Eq. 27)
+  C uxl, uyl;             // low parts of U (U = ux + uxl to FP64 accuracy)
   C lam_s, T0;
   int id, k;              // particle id; index of this tile in its partial slots
+  int rx, ry;             // first tile of the particle's range
 };
 
 // Integer classification of cell (il, jl) of the tile against one disk.
