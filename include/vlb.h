@@ -183,6 +183,25 @@ vlb_status vlb_get_audit(vlb_handle* h, double* total_mass, double* total_eps, d
 vlb_status vlb_get_solid_fraction(vlb_handle* h, uint8_t* count, int32_t* owner, uint8_t* flag,
                                   double* fsp);
 
+/* Allocation-free variant of vlb_get_solid_fraction (the paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory during a run -- e.g. while a caching allocator or memory pool owns
+ * the device, or where cudaMalloc/cudaFree would synchronise the device).
+ * Same outputs as vlb_get_solid_fraction, but the dump's scratch lives in one
+ * static device array of the library instead of cudaMalloc'd buffers.
+ *   - At most VLB_NOALLOC_MAX_CELLS cells; a larger lattice gives VLB_EINVAL.
+ *   - The handle must already hold its initial state (vlb_step(h, 0) or any
+ *     step), because building it allocates: otherwise VLB_ESTATE.
+ *   - Every GPU that loads the library holds the array (about 3.5 MB) until
+ *     the process exits; all calls share it and it keeps the last call's
+ *     contents (each call overwrites everything it reads back).
+ *   - Calls that overlap on the GPU race on the array: serialise them.
+ *   - The first call on a device looks the array up with
+ *     cudaGetSymbolAddress; make it before any stream capture. */
+#define VLB_NOALLOC_MAX_CELLS 65536
+vlb_status vlb_get_solid_fraction_noalloc(vlb_handle* h, uint8_t* count, int32_t* owner, uint8_t* flag,
+                                          double* fsp);
+
 /* Contact pair list of the current level: pairs (i, j), i < j, with
  * |X_i - X_j| < R_i + R_j + zeta, in ascending (i, j) order, written as
  * pairs[2k], pairs[2k+1] for k < min(*npairs, capacity).  *npairs receives

@@ -648,3 +648,35 @@ void vlb_destroy(vlb_handle* h) {
 
 }  // extern "C"
 
+// ---- helpers of the allocation-free entry point (vlb_noalloc.cu) ------------
+
+int64_t vlb_cells_of(const vlb_handle* h) { return (int64_t)h->nx * h->ny; }
+
+vlb_status vlb_fail_einval(vlb_handle* h, const char* msg) { return fail(h, VLB_EINVAL, msg); }
+
+vlb_status vlb_fail_cuda(vlb_handle* h, cudaError_t e, const char* where) { return cuda_fail(h, e, where); }
+
+// The solid-fraction dump of the current level into caller-provided device
+// buffers, then to the host arrays.  Allocates nothing; with
+// require_initialized it refuses a handle whose initial state (which
+// allocates) has not been built yet.
+vlb_status vlb_solid_fraction_into(vlb_handle* h, unsigned char* d_count, int* d_owner, unsigned char* d_flag,
+                                   double* d_fsp, uint8_t* count, int32_t* owner, uint8_t* flag, double* fsp,
+                                   bool require_initialized) {
+  if (require_initialized && !h->initialized)
+    return fail(h, VLB_ESTATE, "the handle has no initial state yet: call vlb_step(h, 0) first");
+  const size_t ncell = (size_t)h->nx * h->ny;
+  cudaError_t e = h->p.precision == VLB_FP64
+                      ? launch_raster_dump_f64(h->K64, h->P, h->TL[h->tl], d_count, d_owner, d_flag, d_fsp,
+                                               h->err_dev, h->stream)
+                      : launch_raster_dump_f32(h->K32, h->P, h->TL[h->tl], d_count, d_owner, d_flag, d_fsp,
+                                               h->err_dev, h->stream);
+  if (e == cudaSuccess) e = pull_flags(h);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && count) e = cudaMemcpy(count, d_count, ncell, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && flag) e = cudaMemcpy(flag, d_flag, 4 * ncell, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && owner) e = cudaMemcpy(owner, d_owner, 4 * ncell * sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && fsp) e = cudaMemcpy(fsp, d_fsp, 4 * ncell * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "solid fraction dump (no allocation)");
+  return device_flags(h);
+}

@@ -84,6 +84,8 @@ def _load():
         "vlb_get_audit": (ctypes.c_int, [h, d, d, d]),
         "vlb_get_solid_fraction": (ctypes.c_int, [h, P(ctypes.c_uint8), P(ctypes.c_int32),
                                                   P(ctypes.c_uint8), d]),
+        "vlb_get_solid_fraction_noalloc": (ctypes.c_int, [h, P(ctypes.c_uint8), P(ctypes.c_int32),
+                                                          P(ctypes.c_uint8), d]),
         "vlb_get_contact_pairs": (ctypes.c_int, [h, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]),
         "vlb_profile_begin": (ctypes.c_int, [h, ctypes.c_int32]),
         "vlb_profile_end": (ctypes.c_int, [h, d, P(ctypes.c_int32), P(ctypes.c_int32)]),
@@ -206,6 +208,23 @@ def vlb_get_solid_fraction(h, nx: int, ny: int):
     fsp = np.empty((ny, nx, 4), dtype=np.float64)
     _check(_lib.vlb_get_solid_fraction(h, _ptr(count, ctypes.c_uint8), _ptr(owner, ctypes.c_int32),
                                        _ptr(flag, ctypes.c_uint8), _ptr(fsp)), h)
+    return count, owner, flag, fsp
+
+
+VLB_NOALLOC_MAX_CELLS = 65536
+
+
+def vlb_get_solid_fraction_noalloc(h, nx: int, ny: int):
+    """Same outputs as vlb_get_solid_fraction, from the library's static
+    device scratch instead of per-call device allocations (see include/vlb.h
+    for the limits: at most VLB_NOALLOC_MAX_CELLS cells, initialised handle,
+    calls must not overlap on the GPU)."""
+    count = np.empty((ny, nx), dtype=np.uint8)
+    owner = np.empty((ny, nx, 4), dtype=np.int32)
+    flag = np.empty((ny, nx, 4), dtype=np.uint8)
+    fsp = np.empty((ny, nx, 4), dtype=np.float64)
+    _check(_lib.vlb_get_solid_fraction_noalloc(h, _ptr(count, ctypes.c_uint8), _ptr(owner, ctypes.c_int32),
+                                               _ptr(flag, ctypes.c_uint8), _ptr(fsp)), h)
     return count, owner, flag, fsp
 
 
