@@ -25,7 +25,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_CELL = {"fp32": 152, "fp64": 304}  # f and g read + write, S read + write
+# f and g read + write (18 populations each way) plus S read + write (FP32, or FP64)
+BYTES_PER_CELL = {"fp32": 152, "fp64": 304, "fp16": 80, "bf16": 80}
 METRIC = "coupled flow+thermal MLUPS"
 UNIT = "MLUPS"
 
@@ -123,7 +124,8 @@ def _make_case(args):
 
 def _params(case, V):
     prm = {k: v for k, v in case.params.items() if k != "precision"}
-    prec = V.VLB_FP64 if case.params["precision"] == "fp64" else V.VLB_FP32
+    prec = {"fp64": V.VLB_FP64, "fp32": V.VLB_FP32, "fp16": V.VLB_FP16_STORE,
+            "bf16": V.VLB_BF16_STORE}[case.params["precision"]]
     return V.vlb_params_default(precision=prec, max_particles=len(case.x), **prm)
 
 
@@ -215,7 +217,8 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64",
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f16 storage / f32", "bf16": "bf16 storage / f32"}[
+            args.precision],
         "data": "synthetic (seeded SplitMix64 placement)",
         "config": {"workload": case.name, "cells": cells, "particles": len(case.x),
                    "storage": args.precision, "parallelism": f"replicas x{world}",
@@ -343,7 +346,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=2048)
     ap.add_argument("--particles", type=int, default=2048)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

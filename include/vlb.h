@@ -61,8 +61,9 @@ typedef enum {
 typedef enum {
   VLB_FP64 = 0,        /* FP64 storage and arithmetic */
   VLB_FP32 = 1,        /* FP32 storage and arithmetic */
-  VLB_FP16_STORE = 2,  /* reserved: FP16 storage, FP32 arithmetic */
-  VLB_BF16_STORE = 3   /* reserved: BF16 storage, FP32 arithmetic */
+  VLB_FP16_STORE = 2,  /* FP16 storage of the populations (as deviations from the rest
+                          equilibrium), FP32 arithmetic; FP64 particle sums and integration */
+  VLB_BF16_STORE = 3   /* the same with BF16 storage */
 } vlb_precision;
 
 typedef enum { VLB_WALL_ADIABATIC = 0, VLB_WALL_DIRICHLET = 1 } vlb_thermal_wall;
@@ -122,7 +123,7 @@ vlb_status vlb_params_default(vlb_params* p);
 /* Allocate a lattice of p->nx * p->ny cells on the current CUDA device and
  * its particle arrays.  *out receives the handle (NULL on failure).  Errors:
  * VLB_EINVAL for inconsistent parameters (tau_f <= 1/2, ratios <= 0, bad
- * sizes, unsupported precision), VLB_ENOMEM, VLB_ECUDA. */
+ * sizes, unknown precision), VLB_ENOMEM, VLB_ECUDA. */
 vlb_status vlb_create(const vlb_params* p, vlb_handle** out);
 
 /* Queue all further work of h on cuda_stream (a cudaStream_t; NULL selects

@@ -10,6 +10,7 @@
 //                      level n+1, and clears list buffer 1 - b for the next step
 // The first step is preceded by the initial state (lattice INIT mode).
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,7 +31,9 @@ struct vlb_handle {
   bool own_stream = false;
   int nx = 0, ny = 0, pitch = 0, ntx = 0, nty = 0;
   long long plane = 0;
-  size_t esize = 0;          // bytes per stored population / arithmetic value
+  size_t ssize = 0;          // bytes per stored population
+  size_t esize = 0;          // bytes per arithmetic value (S and macroscopic planes)
+  int storage = 0;           // STORE_* of the FP32-arithmetic kernels
   void* pop[2] = {nullptr, nullptr};
   void* spl[2] = {nullptr, nullptr};
   void* macro = nullptr;
@@ -159,8 +162,6 @@ static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
   K.sj_f = C(1.0 / tgf);
   K.se_f = C(p.thermal_rates_mode == 0 ? 1.0 / (0.5 + 0.25 / (tgf - 0.5)) : 1.0);
   K.gk_f = C(-3.0 / (cref * tgf));
-  const double dv[4] = {9.0, 36.0, 6.0, 12.0};
-  for (int k = 0; k < 4; ++k) K.rcp[k] = C(1.0 / dv[k]);
 }
 
 extern "C" {
@@ -199,8 +200,8 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     return fail(nullptr, VLB_EINVAL, "rho_ratio, cv_ratio, k_ratio_default must be positive");
   if (!(p.contact_range > 0.0) || !(p.contact_eps_p > 0.0) || !(p.contact_eps_w > 0.0))
     return fail(nullptr, VLB_EINVAL, "contact parameters must be positive");
-  if (p.precision != VLB_FP32 && p.precision != VLB_FP64)
-    return fail(nullptr, VLB_EINVAL, "precision not supported by this build (FP32, FP64)");
+  if (p.precision < VLB_FP64 || p.precision > VLB_BF16_STORE)
+    return fail(nullptr, VLB_EINVAL, "precision must be a vlb_precision value");
   if (p.max_particles < 0 || p.max_particles > (1 << 24)) return fail(nullptr, VLB_EINVAL, "max_particles");
   if (p.thermal_rates_mode != 0 && p.thermal_rates_mode != 1)
     return fail(nullptr, VLB_EINVAL, "thermal_rates_mode must be 0 or 1");
@@ -215,7 +216,9 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   h->nx = p.nx;
   h->ny = p.ny;
   h->esize = p.precision == VLB_FP64 ? 8 : 4;
-  const int align = 128 / (int)h->esize;
+  h->ssize = p.precision == VLB_FP64 ? 8 : (p.precision == VLB_FP32 ? 4 : 2);
+  h->storage = p.precision == VLB_FP16_STORE ? STORE_F16 : (p.precision == VLB_BF16_STORE ? STORE_BF16 : STORE_F32);
+  const int align = 128 / (int)h->ssize;
   h->pitch = (p.nx + align - 1) / align * align;
   h->plane = (long long)h->pitch * p.ny;
   if (h->plane >= (1ll << 31)) {
@@ -234,7 +237,7 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
   h->own_stream = true;
-  const size_t popbytes = (size_t)18 * h->plane * h->esize;
+  const size_t popbytes = (size_t)18 * h->plane * h->ssize;
   for (int b = 0; b < 2; ++b) {
     if ((e = cudaMalloc(&h->pop[b], popbytes)) != cudaSuccess) return bail(e, "populations");
     if ((e = cudaMalloc(&h->spl[b], (size_t)h->plane * h->esize)) != cudaSuccess) return bail(e, "S plane");
@@ -247,14 +250,15 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     if ((e = cudaMalloc(&h->TL[b].ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
     cudaMemsetAsync(h->TL[b].count, 0, ntiles * sizeof(int), h->stream);
   }
-  // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints and 2 NBR_CAP
-  // doubles per particle; every sub-array starts on a 256-byte boundary (int4
-  // loads need 16-byte alignment)
+  // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints, 2 NBR_CAP + 8
+  // doubles and one raster record per particle; every sub-array starts on a
+  // 256-byte boundary (int4 and record loads need 16-byte alignment)
   const size_t capn = (size_t)std::max(h->cap, 1);
   auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t pbytes = 15 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) +
                         a256(capn * sizeof(int)) + a256(capn * NBR_CAP * sizeof(int)) +
-                        a256(capn * NBR_CAP * 2 * sizeof(double));
+                        a256(capn * NBR_CAP * 2 * sizeof(double)) + a256(capn * 8 * sizeof(double)) +
+                        a256(capn * sizeof(RasterRec));
   if ((e = cudaMalloc(&h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
   {
     char* b = static_cast<char*>(h->pbase);
@@ -265,7 +269,9 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     h->P.prange = reinterpret_cast<int4*>(b); b += a256(capn * sizeof(int4));
     h->P.nbr_count = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.nbr = reinterpret_cast<int*>(b); b += a256(capn * NBR_CAP * sizeof(int));
-    h->P.nbr_f = reinterpret_cast<double*>(b);
+    h->P.nbr_f = reinterpret_cast<double*>(b); b += a256(capn * NBR_CAP * 2 * sizeof(double));
+    h->P.pk = reinterpret_cast<double*>(b); b += a256(capn * 8 * sizeof(double));
+    h->P.rec = reinterpret_cast<RasterRec*>(b);
   }
   cudaMemsetAsync(h->pbase, 0, pbytes, h->stream);
   h->audit_blocks = 608;  // 4 x 152 SMs
@@ -349,7 +355,7 @@ static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_b
   TileLists TL = h->TL[lists];
   TL.next_count = mode == MODE_MACROS ? nullptr : h->TL[1 - lists].count;
   cudaError_t e = h->p.precision == VLB_FP64 ? launch_lattice_f64(mode, h->K64, B, h->P, TL, h->stream)
-                                             : launch_lattice_f32(mode, h->K32, B, h->P, TL, h->stream);
+                                             : launch_lattice_f32(mode, h->K32, B, h->P, TL, h->stream, h->storage);
   if (e != cudaSuccess) return cuda_fail(h, e, "lattice kernel");
   return VLB_OK;
 }
@@ -381,10 +387,26 @@ static vlb_status initialize(vlb_handle* h) {
     CK(h, cudaMemcpyAsync(h->P.ux_prev, h->hux.data(), b, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->P.uy_prev, h->huy.data(), b, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->P.om_prev, h->hom.data(), b, cudaMemcpyHostToDevice, h->stream));
+    // per-particle constants of Eqs. 26, 29 (disk, rho_f = 1) and the wall contact factor
+    std::vector<double> pk((size_t)8 * n, 0.0);
+    const double gmag = std::hypot(p.gravity[0], p.gravity[1]);
+    const double cscale = std::fabs(p.rho_ratio - 1.0) * gmag * M_PI;
+    for (int k = 0; k < n; ++k) {
+      const double R = h->hr[k], area = M_PI * R * R;
+      const double M = p.rho_ratio * area, I = 0.5 * M * R * R;
+      pk[8 * k + 0] = 1.0 / M;
+      pk[8 * k + 1] = 1.0 / I;
+      pk[8 * k + 2] = area;                 // M_in = rho_f M / rho_s
+      pk[8 * k + 3] = 0.5 * area * R * R;   // I_in
+      pk[8 * k + 4] = (p.rho_ratio - 1.0) * area;
+      pk[8 * k + 5] = cscale * R * R / p.contact_eps_w;
+    }
+    CK(h, cudaMemcpyAsync(h->P.pk, pk.data(), pk.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));  // host vectors may be reused below
   }
   fill_const(h, h->K32);
   fill_const(h, h->K64);
+
   ParticleConst& c = h->PC;
   c.np = n; c.nx = h->nx; c.ny = h->ny; c.per_x = p.periodic[0]; c.per_y = p.periodic[1];
   c.ntx = h->ntx; c.nty = h->nty; c.kt = h->kt;
@@ -392,6 +414,7 @@ static vlb_status initialize(vlb_handle* h) {
   c.zeta = p.contact_range; c.eps_p = p.contact_eps_p; c.eps_w = p.contact_eps_w;
   c.contact_scale = std::fabs(p.rho_ratio - 1.0) * std::hypot(p.gravity[0], p.gravity[1]) * M_PI;
   c.margin = margin;
+  c.inv_zeta = 1.0 / p.contact_range;
   h->K32.zeta = h->K64.zeta = p.contact_range;
   h->K32.contact_scale = h->K64.contact_scale = c.contact_scale;
   h->K32.eps_p = h->K64.eps_p = p.contact_eps_p;
@@ -537,7 +560,7 @@ vlb_status vlb_get_audit(vlb_handle* h, double* total_mass, double* total_eps, d
                       ? launch_audit_f64(h->K64, h->pop[h->cur], h->macro, h->audit_scratch, h->audit_blocks,
                                          h->audit_out, h->err_dev, h->stream)
                       : launch_audit_f32(h->K32, h->pop[h->cur], h->macro, h->audit_scratch, h->audit_blocks,
-                                         h->audit_out, h->err_dev, h->stream);
+                                         h->audit_out, h->err_dev, h->stream, h->storage);
   if (e != cudaSuccess) return cuda_fail(h, e, "audit");
   double o[3];
   CK(h, cudaMemcpyAsync(o, h->audit_out, sizeof(o), cudaMemcpyDeviceToHost, h->stream));

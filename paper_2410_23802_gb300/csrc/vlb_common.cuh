@@ -53,6 +53,19 @@ enum : int { MODE_INIT = 0, MODE_STEP = 1, MODE_MACROS = 2 };
 // ---------------------------------------------------------------------------
 // Particle arrays (SoA, FP64) -- Sec. 2.3.
 // ---------------------------------------------------------------------------
+// What the FP32 lattice kernel needs of one particle, prepared once per step
+// by the particle kernel so that the lattice kernel does no FP64 arithmetic.
+// Centre: cell index (xi, yi) plus the fraction X - xi as an unevaluated FP32
+// sum xfh + xfl and as a 2^-20 fixed-point offset qfx.
+struct alignas(16) RasterRec {
+  int xi, yi, qfx, qfy;
+  long long rq2;               // (R rounded to 2^-20)^2, fixed point
+  float xfh, xfl, yfh, yfl;
+  float r, far2, near2;        // radius; quick-reject bounds on the centre distance^2
+  float ux, uxl, uy, uyl, om;  // U as hi + lo, Omega
+  float lam_s, T0;
+};
+
 struct ParticleArrays {
   double *x, *y, *theta, *ux, *uy, *om;
   double *ux_prev, *uy_prev, *om_prev;
@@ -63,6 +76,8 @@ struct ParticleArrays {
   int* nbr_count;          // contact partners per particle
   int* nbr;                // [n][NBR_CAP], unordered (sorted where used)
   double* nbr_f;           // [n][NBR_CAP][2] contact force on the particle from that partner
+  double* pk;              // [n][8] constants: 1/M, 1/I, M_in, I_in, body force factor, wall factor
+  RasterRec* rec;          // [n] raster records of the current level
 };
 
 struct TileLists {
@@ -100,8 +115,6 @@ struct LatticeConst {
   C bx, by, T_ref, T_fluid;  // buoyancy b = -rho_f beta g; T_f = initial fluid temperature
   C dT_ref;                  // T_f - T_ref
   C tau_gf, sj_f, se_f, gk_f;  // thermal rates of a fluid cell (Eqs. 18, 22, 23)
-  // rounded 1/9, 1/36, 1/6, 1/12 of M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
-  C rcp[4];
   C wall_dT[4];              // T_w - T_f per side
 };
 

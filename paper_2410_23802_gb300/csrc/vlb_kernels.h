@@ -11,10 +11,14 @@ struct ParticleConst {
   double rho_ratio, gx, gy;
   double zeta, eps_p, eps_w, contact_scale;  // scale = |rho_r - 1| rho_f |g| pi
   double margin;                             // tile-range margin around each disk (cells)
+  double inv_zeta;                           // 1 / zeta
 };
 
+// Storage of the populations of the FP32-arithmetic kernels.
+enum : int { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
+
 cudaError_t launch_lattice_f32(int mode, const LatticeConst<float>& K, const StepBuffers& B,
-                               const ParticleArrays& P, const TileLists& TL, cudaStream_t st);
+                               const ParticleArrays& P, const TileLists& TL, cudaStream_t st, int storage);
 cudaError_t launch_lattice_f64(int mode, const LatticeConst<double>& K, const StepBuffers& B,
                                const ParticleArrays& P, const TileLists& TL, cudaStream_t st);
 
@@ -37,7 +41,8 @@ cudaError_t launch_particle_bin(const ParticleConst& c, const ParticleArrays& P,
 // FP64 audits: out[0] = sum f, out[1] = sum eps, out[2] = sum g (block partials
 // in scratch[3 * nblocks], summed in block order).
 cudaError_t launch_audit_f32(const LatticeConst<float>& K, const void* pop, const void* macro,
-                             double* scratch, int nblocks, double* out, unsigned* err, cudaStream_t st);
+                             double* scratch, int nblocks, double* out, unsigned* err, cudaStream_t st,
+                             int storage);
 cudaError_t launch_audit_f64(const LatticeConst<double>& K, const void* pop, const void* macro,
                              double* scratch, int nblocks, double* out, unsigned* err, cudaStream_t st);
 

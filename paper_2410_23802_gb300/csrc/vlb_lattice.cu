@@ -12,29 +12,33 @@
 // rows padded to 128 B.  f is stored as the deviation from the rest
 // equilibrium w_i, g as the deviation from g^eq(T_fluid) (g_off), S in the
 // arithmetic type.  Populations ping-pong between two buffers.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "vlb_common.cuh"
 #include "vlb_raster.cuh"
 #include "vlb_kernels.h"
 
 namespace vlb {
 
+// Population loads and streaming stores for FP64, FP32, FP16 and BF16 storage
+// (16-bit values are converted to and from FP32 with round-to-nearest-even).
 template <class C, class S>
 __device__ __forceinline__ C load_pop(const S* p) { return C(__ldg(p)); }
+template <>
+__device__ __forceinline__ float load_pop<float, __half>(const __half* p) { return __half2float(__ldg(p)); }
+template <>
+__device__ __forceinline__ float load_pop<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
 
 template <class C, class S>
 __device__ __forceinline__ void store_pop(S* p, C v) { __stcs(p, S(v)); }
-
-// b / d for d = 9, 36, 6, 12 (index k), correctly rounded: q0 = b r, then one
-// correction with the exact residual b - d q0.  For FP32 this equals IEEE
-// division for every input of magnitude >= 2^-119 (checked exhaustively for
-// these four divisors).  Correct rounding matters: a steady state maps
-// d * (b / d) back to b, whereas a plain reciprocal product perturbs it every
-// step, and identical cells (a solid interior) add such errors up coherently.
-template <class C>
-__device__ __forceinline__ C rdiv(C b, const LatticeConst<C>& K, int k) {
-  const C d = k == 0 ? C(9) : (k == 1 ? C(36) : (k == 2 ? C(6) : C(12)));
-  const C q0 = b * K.rcp[k];
-  return fma(fma(-d, q0, b), K.rcp[k], q0);
+template <>
+__device__ __forceinline__ void store_pop<float, __half>(__half* p, float v) { __stcs(p, __float2half_rn(v)); }
+template <>
+__device__ __forceinline__ void store_pop<float, __nv_bfloat16>(__nv_bfloat16* p, float v) {
+  __stcs(p, __float2bfloat16_rn(v));
 }
 
 template <class C>
@@ -44,41 +48,62 @@ __device__ __forceinline__ C warp_sum(C v) {
   return v;
 }
 
+// Shared memory of one tile: its particles and the per-row exchange sums.
+template <class C>
+struct TileShared {
+  PartTile<C> p[TILE_CAP];
+  C red[TILE_Y][TILE_CAP][3];
+};
+
 // Particle list of one tile, sorted by id (rank sort; ids are unique), with
 // each particle's geometry relative to the tile origin.  Returns the count.
+// Every thread reads the count itself, so a tile without particles passes no
+// barrier; otherwise one barrier publishes the records.
 template <class C>
 __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArrays& P, const TileLists& TL,
-                                   int tile_x, int tile_y, int* s_n, int* s_raw, PartTile<C>* s_p) {
+                                   int tile_x, int tile_y, TileShared<C>& sh) {
+  PartTile<C>* s_p = sh.p;
   const int tid = threadIdx.y * TILE_X + threadIdx.x;
   const int tile = tile_y * K.ntx + tile_x;
   const int x0 = tile_x * TILE_X, y0 = tile_y * TILE_Y;
-  if (tid == 0) {
-    const int c = TL.count[tile];
-    *s_n = c < TILE_CAP ? c : TILE_CAP;
-  }
-  __syncthreads();
-  const int np = *s_n;
-  if (tid < np) s_raw[tid] = TL.ids[(long long)tile * TILE_CAP + tid];
-  __syncthreads();
+  const int c = TL.count[tile];
+  const int np = c < TILE_CAP ? c : TILE_CAP;
+  if (np == 0) return 0;
   if (tid < np) {
-    const int id = s_raw[tid];
+    const int* ids = TL.ids + (long long)tile * TILE_CAP;
+    const int id = ids[tid];
     int rank = 0;
-    for (int k = 0; k < np; ++k) rank += s_raw[k] < id;
+    for (int k = 0; k < np; ++k) rank += ids[k] < id;
     PartTile<C> q;
-    const double X = P.x[id] - double(x0), Y = P.y[id] - double(y0), R = P.r[id];
-    const long long Q = 1ll << QBITS;
-    q.xq = __double2ll_rn(P.x[id] * double(Q)) - (long long)x0 * Q;
-    q.yq = __double2ll_rn(P.y[id] * double(Q)) - (long long)y0 * Q;
-    const long long rq = __double2ll_rn(R * double(Q));
-    q.rq2 = rq * rq;
-    q.xh = C(X); q.xl = C(X - double(q.xh));
-    q.yh = C(Y); q.yl = C(Y - double(q.yh));
-    q.r = C(R);
-    q.far2 = C((R + 0.75) * (R + 0.75));
-    q.near2 = R > 0.75 ? C((R - 0.75) * (R - 0.75)) : C(-1);
-    q.ux = C(P.ux[id]); q.uy = C(P.uy[id]); q.om = C(P.om[id]);
-    q.uxl = C(P.ux[id] - double(q.ux)); q.uyl = C(P.uy[id] - double(q.uy));
-    q.lam_s = C(P.lam_s[id]); q.T0 = C(P.T0[id]);
+    if (sizeof(C) == 4) {
+      // FP32 kernel: the particle kernel's raster record, no FP64 arithmetic
+      const RasterRec rc = P.rec[id];
+      const long long Q = 1ll << QBITS;
+      q.xq = (long long)(rc.xi - x0) * Q + rc.qfx;
+      q.yq = (long long)(rc.yi - y0) * Q + rc.qfy;
+      q.rq2 = rc.rq2;
+      const C fx = C(rc.xi - x0), fy = C(rc.yi - y0);  // exact small integers
+      q.xh = fx + C(rc.xfh); q.xl = ((fx - q.xh) + C(rc.xfh)) + C(rc.xfl);
+      q.yh = fy + C(rc.yfh); q.yl = ((fy - q.yh) + C(rc.yfh)) + C(rc.yfl);
+      q.r = C(rc.r); q.far2 = C(rc.far2); q.near2 = C(rc.near2);
+      q.ux = C(rc.ux); q.uxl = C(rc.uxl); q.uy = C(rc.uy); q.uyl = C(rc.uyl); q.om = C(rc.om);
+      q.lam_s = C(rc.lam_s); q.T0 = C(rc.T0);
+    } else {
+      const double X = P.x[id] - double(x0), Y = P.y[id] - double(y0), R = P.r[id];
+      const long long Q = 1ll << QBITS;
+      q.xq = __double2ll_rn(P.x[id] * double(Q)) - (long long)x0 * Q;
+      q.yq = __double2ll_rn(P.y[id] * double(Q)) - (long long)y0 * Q;
+      const long long rq = __double2ll_rn(R * double(Q));
+      q.rq2 = rq * rq;
+      q.xh = C(X); q.xl = C(X - double(q.xh));
+      q.yh = C(Y); q.yl = C(Y - double(q.yh));
+      q.r = C(R);
+      q.far2 = C((R + 0.75) * (R + 0.75));
+      q.near2 = R > 0.75 ? C((R - 0.75) * (R - 0.75)) : C(-1);
+      q.ux = C(P.ux[id]); q.uy = C(P.uy[id]); q.om = C(P.om[id]);
+      q.uxl = C(P.ux[id] - double(q.ux)); q.uyl = C(P.uy[id] - double(q.uy));
+      q.lam_s = C(P.lam_s[id]); q.T0 = C(P.T0[id]);
+    }
     q.id = id;
     const int4 rg = P.prange[id];
     const int kx = tile_x - rg.x, ky = tile_y - rg.y;
@@ -128,25 +153,16 @@ __device__ __forceinline__ C raster_cell(int tx, int ty, int np, const PartTile<
 #define VLB_LATTICE_MIN_BLOCKS 4
 #endif
 
+// Pull streaming of one cell (Eqs. 3b, 17b) with the wall rules: f-bar and
+// g-bar of x - e_i, or the bounced value at a wall; S of level n.
 template <class S, class C, int MODE>
-__global__ void __launch_bounds__(TILE_X * TILE_Y, sizeof(C) == 4 ? VLB_LATTICE_MIN_BLOCKS : 1)
-lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArrays P, const TileLists TL) {
-  __shared__ int s_n;
-  __shared__ int s_raw[TILE_CAP];
-  __shared__ PartTile<C> s_p[TILE_CAP];
-  __shared__ C s_red[TILE_Y][TILE_CAP][3];
-
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * TILE_X + tx;
-  const int tile_x = blockIdx.x, tile_y = blockIdx.y;
-  const int x = tile_x * TILE_X + tx, y = tile_y * TILE_Y + ty;
+__device__ __forceinline__ void pull_direct(const LatticeConst<C>& K, const StepBuffers& B, int tile_x, int tile_y,
+                                            C (&f)[9], C (&g)[9], C& s_old) {
+  const int x = tile_x * TILE_X + threadIdx.x, y = tile_y * TILE_Y + threadIdx.y;
   const bool active = (x < K.nx) && (y < K.ny);
   const int cell = y * K.pitch + x;
   const S* __restrict__ src = static_cast<const S*>(B.src);
-
-  // ---- streaming (pull) with wall rules, issued first ------------------------
-  C f[9], g[9];
-  C s_old = C(0);
+  s_old = C(0);
   if (MODE == MODE_INIT) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) { f[i] = C(0); g[i] = C(0); }
@@ -190,15 +206,32 @@ lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArray
     for (int i = 0; i < 9; ++i) { f[i] = C(0); g[i] = C(0); }
   }
 
+}
+
+// Everything of one time step at one cell after the pull: the tile's particle
+// list, f_s and owners, correction, thermal macroscopics, exchange partials,
+// both collisions and the stores.  Called by every thread of the CTA (it has
+// barriers); returns the tile's particle count.
+template <class S, class C, int MODE>
+__device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuffers& B, const ParticleArrays& P,
+                                         const TileLists& TL, int tile_x, int tile_y, C (&f)[9], C (&g)[9],
+                                         const C s_old, TileShared<C>& sh) {
+  const PartTile<C>* s_p = sh.p;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TILE_X + tx;
+  const int x = tile_x * TILE_X + tx, y = tile_y * TILE_Y + ty;
+  const bool active = (x < K.nx) && (y < K.ny);
+  const int cell = y * K.pitch + x;
+
   // ---- particle list of the tile (loads above are in flight) ----------------
-  const int np = load_tile_particles<C>(K, P, TL, tile_x, tile_y, &s_n, s_raw, s_p);
+  const int np = load_tile_particles<C>(K, P, TL, tile_x, tile_y, sh);
   if (MODE != MODE_MACROS) {
     // the other list buffer is filled by the next particle step
     if (tid == 0 && TL.next_count != nullptr) TL.next_count[tile_y * K.ntx + tile_x] = 0;
     // contact partners of the particles of this tile (Sec. 2.3): each pair is
     // tested in the first tile both ranges share, and appended to both lists
     for (int t = tid; t < np * np; t += TILE_X * TILE_Y) {
-      const int a = t / np, b = t - a * np;
+      const int a = t / max(np, 1), b = t - a * np;
       if (b <= a) continue;
       const PartTile<C>& qa = s_p[a];
       const PartTile<C>& qb = s_p[b];
@@ -231,6 +264,7 @@ lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArray
       }
       if (si >= NBR_CAP || sj >= NBR_CAP) atomicOr(B.err, ERR_NBR_OVERFLOW);
     }
+
   }
 
   // ---- solid fraction and owners (Sec. 2) -----------------------------------
@@ -255,9 +289,7 @@ lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArray
   C jy = (f[2] - f[4]) + (d57 - d86);
   const C rho = C(1) + drho;
   const C inv_rho = C(1) / rho;
-  C mesF[MAX_OWNERS][3];
-#pragma unroll
-  for (int k = 0; k < MAX_OWNERS; ++k) { mesF[k][0] = mesF[k][1] = mesF[k][2] = C(0); }
+  const C jxs = jx, jys = jy;  // j* before the correction (for the exchange term)
   C lam = (C(1) - fs) * K.lam_f;
   C dT_init = C(0);  // sum_p f_s,p c_vs (T0_p - T_f): eps^0 - c_v T_f of the mixing rule
   if (nown > 0) {
@@ -281,13 +313,6 @@ lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArray
         const C eu = C(ex(i)) * usx + C(ey(i)) * usy;
         pf[i] += w * (C(3) * eu + C(4.5) * eu * eu - C(1.5) * u2);
       }
-      // sum_i e_i f_i^eq(rho, u_s) = rho u_s; Delta F = -f_s,p (rho u_s - j*),
-      // formed as (U_hi - j*) + (U_lo + Omega x r) + drho u_s
-      const C dFx = -w * (((q.ux - jx) + (q.uxl + rotx)) + drho * usx);
-      const C dFy = -w * (((q.uy - jy) + (q.uyl + roty)) + drho * usy);
-      mesF[k][0] = dFx;
-      mesF[k][1] = dFy;
-      mesF[k][2] = rx * dFy - ry * dFx;
       cjx += w * rho * usx;
       cjy += w * rho * usy;
       lam += w * q.lam_s;
@@ -376,38 +401,53 @@ lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArray
         bool mine = false;
 #pragma unroll
         for (int k = 0; k < MAX_OWNERS; ++k)
-          if (own[k] == sl) { v0 = mesF[k][0]; v1 = mesF[k][1]; v2 = mesF[k][2]; mine = true; }
+          if (own[k] == sl) {
+            // sum_i e_i f_i^eq(rho, u_s) = rho u_s; Delta F = -f_s,p (rho u_s - j*),
+            // formed as (U_hi - j*) + (U_lo + Omega x r) + drho u_s (Eq. 28)
+            const PartTile<C>& q = s_p[sl];
+            const C rx = ((C(tx) + C(0.5)) - q.xh) - q.xl, ry = ((C(ty) + C(0.5)) - q.yh) - q.yl;
+            const C rotx = -q.om * ry, roty = q.om * rx;
+            const C usx = q.ux + (q.uxl + rotx), usy = q.uy + (q.uyl + roty);
+            const C w = ofs[k];
+            v0 = -w * (((q.ux - jxs) + (q.uxl + rotx)) + drho * usx);
+            v1 = -w * (((q.uy - jys) + (q.uyl + roty)) + drho * usy);
+            v2 = rx * v1 - ry * v0;
+            mine = true;
+          }
         if (__any_sync(0xffffffffu, mine)) {
           v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
         }
-        if (tx == 0) { s_red[ty][sl][0] = v0; s_red[ty][sl][1] = v1; s_red[ty][sl][2] = v2; }
+        if (tx == 0) { sh.red[ty][sl][0] = v0; sh.red[ty][sl][1] = v1; sh.red[ty][sl][2] = v2; }
       }
       __syncthreads();
       for (int t = tid; t < 3 * np; t += TILE_X * TILE_Y) {
         const int sl = t / 3, c = t - 3 * sl;
         C acc = C(0);
 #pragma unroll
-        for (int w = 0; w < TILE_Y; ++w) acc += s_red[w][sl][c];
+        for (int w = 0; w < TILE_Y; ++w) acc += sh.red[w][sl][c];
         const PartTile<C>& q = s_p[sl];
         if (q.k >= 0) P.partial[((long long)q.id * K.kt + q.k) * 3 + c] = double(acc);
         else if (c == 0) atomicOr(B.err, ERR_PARTIAL_OVERFLOW);
       }
     }
 
-    if (!active) return;
+    if (!active) return np;
 
     // ---- MRT collision of f in moment space (Eqs. 3a, 4-7) ------------------
+    // Written as f-bar = f + M^-1 (m-bar - m): only the relaxed moments and the
+    // forcing change, and M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6,
+    // 1/12, 1/4, 1/4).  The conserved moments get exactly rho and j + F
+    // (Eq. 9: rho u = j + F/2); in cells the correction touched, whose f carries
+    // FP32-rounded weights, the difference to those targets is put back here
+    // so that no rounding bias repeats step after step.
     {
       const C m1 = -C(4) * f[0] - (f[1] + f[2] + f[3] + f[4]) + C(2) * (f[5] + f[6] + f[7] + f[8]);
       const C m2 = C(4) * f[0] - C(2) * (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
-      const C m3 = jx;
       const C m4 = -C(2) * f[1] + C(2) * f[3] + f[5] - f[6] - f[7] + f[8];
-      const C m5 = jy;
       const C m6 = -C(2) * f[2] + C(2) * f[4] + f[5] + f[6] - f[7] - f[8];
       const C m7 = f[1] - f[2] + f[3] - f[4];
       const C m8 = f[5] - f[6] + f[7] - f[8];
       // deviations of m^eq(rho, u) from m^eq(1, 0) (Eq. 6), with rho u = j + F/2
-      // (Eq. 9) taken directly instead of through u
       const C e3 = jx + C(0.5) * Fx, e5 = jy + C(0.5) * Fy;
       const C ru2 = e3 * ux + e5 * uy;
       const C e1 = -C(2) * drho + C(3) * ru2;
@@ -416,37 +456,43 @@ lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArray
       // forcing moments (Eq. 7)
       const C Fu = Fx * ux + Fy * uy;
       const C F7 = C(2) * (Fx * ux - Fy * uy), F8 = Fx * uy + Fy * ux;
-      const C b0 = drho;
-      const C b1 = m1 - K.s_e * (m1 - e1) + (C(1) - C(0.5) * K.s_e) * (C(6) * Fu);
-      const C b2 = m2 - K.s_eps * (m2 - e2) + (C(1) - C(0.5) * K.s_eps) * (-C(6) * Fu);
-      // conserved momentum: m3 - s_j (m3 - rho u) + (1 - s_j/2) F = j + F for any s_j
-      const C b3 = m3 + Fx;
-      const C b4 = m4 - K.s_q * (m4 + e3) + (C(1) - C(0.5) * K.s_q) * (-Fx);
-      const C b5 = m5 + Fy;
-      const C b6 = m6 - K.s_q * (m6 + e5) + (C(1) - C(0.5) * K.s_q) * (-Fy);
-      const C b7 = m7 - K.s_p * (m7 - e7) + (C(1) - C(0.5) * K.s_p) * F7;
-      const C b8 = m8 - K.s_p * (m8 - e8) + (C(1) - C(0.5) * K.s_p) * F8;
-      // f = M^-1 m = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m
-      const C a0 = rdiv(b0, K, 0), a1 = rdiv(b1, K, 1), a2 = rdiv(b2, K, 1);
-      const C a3 = rdiv(b3, K, 2), a4 = rdiv(b4, K, 3), a5 = rdiv(b5, K, 2);
-      const C a6 = rdiv(b6, K, 3), a7 = b7 * C(0.25), a8 = b8 * C(0.25);
+      const C d1 = -K.s_e * (m1 - e1) + (C(1) - C(0.5) * K.s_e) * (C(6) * Fu);
+      const C d2 = -K.s_eps * (m2 - e2) + (C(1) - C(0.5) * K.s_eps) * (-C(6) * Fu);
+      const C d4 = -K.s_q * (m4 + e3) + (C(1) - C(0.5) * K.s_q) * (-Fx);
+      const C d6 = -K.s_q * (m6 + e5) + (C(1) - C(0.5) * K.s_q) * (-Fy);
+      const C d7 = -K.s_p * (m7 - e7) + (C(1) - C(0.5) * K.s_p) * F7;
+      const C d8 = -K.s_p * (m8 - e8) + (C(1) - C(0.5) * K.s_p) * F8;
+      // conserved moments: m-bar_0 = rho, m-bar_3 = j_x + F_x, m-bar_5 = j_y + F_y
+      C d0 = C(0), d3 = Fx, d5 = Fy;
+      if (nown > 0) {
+        const C n0 = ((f[0] + (f[1] + f[3])) + (f[2] + f[4])) + ((f[5] + f[7]) + (f[6] + f[8]));
+        const C q57 = f[5] - f[7], q86 = f[8] - f[6];
+        d0 = drho - n0;
+        d3 = (jx - ((f[1] - f[3]) + (q57 + q86))) + Fx;
+        d5 = (jy - ((f[2] - f[4]) + (q57 - q86))) + Fy;
+      }
+      const C a0 = d0 * C(1.0 / 9.0), a1 = d1 * C(1.0 / 36.0), a2 = d2 * C(1.0 / 36.0);
+      const C a3 = d3 * C(1.0 / 6.0), a4 = d4 * C(1.0 / 12.0), a5 = d5 * C(1.0 / 6.0);
+      const C a6 = d6 * C(1.0 / 12.0), a7 = d7 * C(0.25), a8 = d8 * C(0.25);
       S* dst = static_cast<S*>(B.dst);
       const C c14 = a0 - a1 - C(2) * a2;
       const C c58 = a0 + C(2) * a1 + a2;
-      store_pop<C>(dst + 0 * K.plane + cell, a0 - C(4) * a1 + C(4) * a2);
-      store_pop<C>(dst + 1 * K.plane + cell, c14 + a3 - C(2) * a4 + a7);
-      store_pop<C>(dst + 2 * K.plane + cell, c14 + a5 - C(2) * a6 - a7);
-      store_pop<C>(dst + 3 * K.plane + cell, c14 - a3 + C(2) * a4 + a7);
-      store_pop<C>(dst + 4 * K.plane + cell, c14 - a5 + C(2) * a6 - a7);
-      store_pop<C>(dst + 5 * K.plane + cell, c58 + a3 + a4 + a5 + a6 + a8);
-      store_pop<C>(dst + 6 * K.plane + cell, c58 - a3 - a4 + a5 + a6 - a8);
-      store_pop<C>(dst + 7 * K.plane + cell, c58 - a3 - a4 - a5 - a6 + a8);
-      store_pop<C>(dst + 8 * K.plane + cell, c58 + a3 + a4 - a5 - a6 - a8);
+      store_pop<C>(dst + 0 * K.plane + cell, f[0] + (a0 - C(4) * a1 + C(4) * a2));
+      store_pop<C>(dst + 1 * K.plane + cell, f[1] + (c14 + a3 - C(2) * a4 + a7));
+      store_pop<C>(dst + 2 * K.plane + cell, f[2] + (c14 + a5 - C(2) * a6 - a7));
+      store_pop<C>(dst + 3 * K.plane + cell, f[3] + (c14 - a3 + C(2) * a4 + a7));
+      store_pop<C>(dst + 4 * K.plane + cell, f[4] + (c14 - a5 + C(2) * a6 - a7));
+      store_pop<C>(dst + 5 * K.plane + cell, f[5] + (c58 + a3 + a4 + a5 + a6 + a8));
+      store_pop<C>(dst + 6 * K.plane + cell, f[6] + (c58 - a3 - a4 + a5 + a6 - a8));
+      store_pop<C>(dst + 7 * K.plane + cell, f[7] + (c58 - a3 - a4 - a5 - a6 + a8));
+      store_pop<C>(dst + 8 * K.plane + cell, f[8] + (c58 + a3 + a4 - a5 - a6 - a8));
     }
 
     // ---- MRT collision of g with the source term (Eqs. 17a, 18-20) ----------
+    // The same delta form: n-bar - n for the relaxed moments and the source;
+    // the conserved moment gets sum g + q_c exactly (sigma_0 = 1 with
+    // eps = sum g + q_c / 2, Eq. 21).
     {
-      const C n0 = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
       const C n1 = -C(4) * g[0] - (g[1] + g[2] + g[3] + g[4]) + C(2) * (g[5] + g[6] + g[7] + g[8]);
       const C n2 = C(4) * g[0] - C(2) * (g[1] + g[2] + g[3] + g[4]) + (g[5] + g[6] + g[7] + g[8]);
       const C n3 = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
@@ -458,30 +504,37 @@ lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArray
       // n^eq = [eps, -4 eps + 2 c_ref T, 4 eps - 3 c_ref T, 0, ...]; q_m = [q, -4q, 4q, 0, ...]
       // (deviations from the moments of g^eq(eps_f, T_f))
       const C ct = K.cref * dT;
-      const C b0 = n0 + qc;  // sigma_0 = 1 with eps = sum g + q_c / 2 (Eq. 21)
-      const C b1 = n1 - se * (n1 - (-C(4) * deps + C(2) * ct)) + (C(1) - C(0.5) * se) * (-C(4) * qc);
-      const C b2 = n2 - se * (n2 - (C(4) * deps - C(3) * ct)) + (C(1) - C(0.5) * se) * (C(4) * qc);
-      const C b3 = (C(1) - sj) * n3, b4 = (C(1) - sj) * n4;
-      const C b5 = (C(1) - sj) * n5, b6 = (C(1) - sj) * n6;
-      const C b7 = (C(1) - se) * n7, b8 = (C(1) - se) * n8;
-      const C a0 = rdiv(b0, K, 0), a1 = rdiv(b1, K, 1), a2 = rdiv(b2, K, 1);
-      const C a3 = rdiv(b3, K, 2), a4 = rdiv(b4, K, 3), a5 = rdiv(b5, K, 2);
-      const C a6 = rdiv(b6, K, 3), a7 = b7 * C(0.25), a8 = b8 * C(0.25);
+      const C d1 = -se * (n1 - (-C(4) * deps + C(2) * ct)) + (C(1) - C(0.5) * se) * (-C(4) * qc);
+      const C d2 = -se * (n2 - (C(4) * deps - C(3) * ct)) + (C(1) - C(0.5) * se) * (C(4) * qc);
+      const C a0 = qc * C(1.0 / 9.0), a1 = d1 * C(1.0 / 36.0), a2 = d2 * C(1.0 / 36.0);
+      const C a3 = -sj * n3 * C(1.0 / 6.0), a4 = -sj * n4 * C(1.0 / 12.0);
+      const C a5 = -sj * n5 * C(1.0 / 6.0), a6 = -sj * n6 * C(1.0 / 12.0);
+      const C a7 = -se * n7 * C(0.25), a8 = -se * n8 * C(0.25);
       S* dst = static_cast<S*>(B.dst) + 9 * K.plane;
       const C c14 = a0 - a1 - C(2) * a2;
       const C c58 = a0 + C(2) * a1 + a2;
-      store_pop<C>(dst + 0 * K.plane + cell, a0 - C(4) * a1 + C(4) * a2);
-      store_pop<C>(dst + 1 * K.plane + cell, c14 + a3 - C(2) * a4 + a7);
-      store_pop<C>(dst + 2 * K.plane + cell, c14 + a5 - C(2) * a6 - a7);
-      store_pop<C>(dst + 3 * K.plane + cell, c14 - a3 + C(2) * a4 + a7);
-      store_pop<C>(dst + 4 * K.plane + cell, c14 - a5 + C(2) * a6 - a7);
-      store_pop<C>(dst + 5 * K.plane + cell, c58 + a3 + a4 + a5 + a6 + a8);
-      store_pop<C>(dst + 6 * K.plane + cell, c58 - a3 - a4 + a5 + a6 - a8);
-      store_pop<C>(dst + 7 * K.plane + cell, c58 - a3 - a4 - a5 - a6 + a8);
-      store_pop<C>(dst + 8 * K.plane + cell, c58 + a3 + a4 - a5 - a6 - a8);
+      store_pop<C>(dst + 0 * K.plane + cell, g[0] + (a0 - C(4) * a1 + C(4) * a2));
+      store_pop<C>(dst + 1 * K.plane + cell, g[1] + (c14 + a3 - C(2) * a4 + a7));
+      store_pop<C>(dst + 2 * K.plane + cell, g[2] + (c14 + a5 - C(2) * a6 - a7));
+      store_pop<C>(dst + 3 * K.plane + cell, g[3] + (c14 - a3 + C(2) * a4 + a7));
+      store_pop<C>(dst + 4 * K.plane + cell, g[4] + (c14 - a5 + C(2) * a6 - a7));
+      store_pop<C>(dst + 5 * K.plane + cell, g[5] + (c58 + a3 + a4 + a5 + a6 + a8));
+      store_pop<C>(dst + 6 * K.plane + cell, g[6] + (c58 - a3 - a4 + a5 + a6 - a8));
+      store_pop<C>(dst + 7 * K.plane + cell, g[7] + (c58 - a3 - a4 - a5 - a6 + a8));
+      store_pop<C>(dst + 8 * K.plane + cell, g[8] + (c58 + a3 + a4 - a5 - a6 - a8));
     }
     static_cast<C*>(B.s_dst)[cell] = C(2) * fs + dfs;
   }
+  return np;
+}
+
+template <class S, class C, int MODE>
+__global__ void __launch_bounds__(TILE_X * TILE_Y, sizeof(C) == 4 ? VLB_LATTICE_MIN_BLOCKS : 1)
+lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArrays P, const TileLists TL) {
+  __shared__ TileShared<C> sh;
+  C f[9], g[9], s_old;
+  pull_direct<S, C, MODE>(K, B, blockIdx.x, blockIdx.y, f, g, s_old);
+  cell_body<S, C, MODE>(K, B, P, TL, blockIdx.x, blockIdx.y, f, g, s_old, sh);
 }
 
 // Ownership of every cell at the current level, from the same raster code as
@@ -490,15 +543,14 @@ template <class C>
 __global__ void __launch_bounds__(TILE_X * TILE_Y)
 raster_dump_kernel(const LatticeConst<C> K, const ParticleArrays P, const TileLists TL, unsigned char* count,
                    int* owner, unsigned char* flag, double* fsp, unsigned* err) {
-  __shared__ int s_n;
-  __shared__ int s_raw[TILE_CAP];
-  __shared__ PartTile<C> s_p[TILE_CAP];
+  __shared__ TileShared<C> sh;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int np = load_tile_particles<C>(K, P, TL, blockIdx.x, blockIdx.y, &s_n, s_raw, s_p);
+  const int np = load_tile_particles<C>(K, P, TL, blockIdx.x, blockIdx.y, sh);
   const int x = blockIdx.x * TILE_X + tx, y = blockIdx.y * TILE_Y + ty;
   if (x >= K.nx || y >= K.ny) return;
   int nown, own[MAX_OWNERS], cls[MAX_OWNERS];
   C ofs[MAX_OWNERS];
+  const PartTile<C>* s_p = sh.p;
   raster_cell<C>(tx, ty, np, s_p, nown, own, cls, ofs, err);
   const long long c = (long long)y * K.nx + x;
   count[c] = (unsigned char)nown;
@@ -526,8 +578,8 @@ __global__ void audit_blocks_kernel(const LatticeConst<C> K, const S* pop, const
     const long long cell = y * K.pitch + x;
     double cf = 1.0;
     for (int i = 0; i < 9; ++i) {
-      const double v = double(pop[(long long)i * K.plane + cell]);
-      const double w = double(pop[(long long)(9 + i) * K.plane + cell]);
+      const double v = double(float(pop[(long long)i * K.plane + cell]));
+      const double w = double(float(pop[(long long)(9 + i) * K.plane + cell]));
       bad |= !(v == v) || !(w == w);
       cf += v;
     }
@@ -566,7 +618,9 @@ static cudaError_t launch_mode(int mode, const LatticeConst<C>& K, const StepBuf
 }
 
 cudaError_t launch_lattice_f32(int mode, const LatticeConst<float>& K, const StepBuffers& B,
-                               const ParticleArrays& P, const TileLists& TL, cudaStream_t st) {
+                               const ParticleArrays& P, const TileLists& TL, cudaStream_t st, int storage) {
+  if (storage == STORE_F16) return launch_mode<__half, float>(mode, K, B, P, TL, st);
+  if (storage == STORE_BF16) return launch_mode<__nv_bfloat16, float>(mode, K, B, P, TL, st);
   return launch_mode<float, float>(mode, K, B, P, TL, st);
 }
 cudaError_t launch_lattice_f64(int mode, const LatticeConst<double>& K, const StepBuffers& B,
@@ -602,7 +656,9 @@ static cudaError_t audit(const LatticeConst<C>& K, const void* pop, const void* 
   return cudaGetLastError();
 }
 cudaError_t launch_audit_f32(const LatticeConst<float>& K, const void* pop, const void* macro, double* scratch,
-                             int nblocks, double* out, unsigned* err, cudaStream_t st) {
+                             int nblocks, double* out, unsigned* err, cudaStream_t st, int storage) {
+  if (storage == STORE_F16) return audit<__half, float>(K, pop, macro, scratch, nblocks, out, err, st);
+  if (storage == STORE_BF16) return audit<__nv_bfloat16, float>(K, pop, macro, scratch, nblocks, out, err, st);
   return audit<float, float>(K, pop, macro, scratch, nblocks, out, err, st);
 }
 cudaError_t launch_audit_f64(const LatticeConst<double>& K, const void* pop, const void* macro,

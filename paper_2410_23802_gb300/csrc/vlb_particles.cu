@@ -1,7 +1,7 @@
 // Particle kernels (Sec. 2.3), one thread per particle, FP64 throughout.
 //
-//   particle_advance: F_MES, T_MES as the ordered sum of the per-tile partials
-//     of Eq. 28; the inside-fluid force and torque of Eq. 29 with backward
+//   particle_advance (one thread per particle): F_MES, T_MES as the
+//     fixed-order sum of the per-tile partials of Eq. 28; the inside-fluid force and torque of Eq. 29 with backward
 //     differences; the short-range contact force; Eqs. 26 and 30 by forward
 //     Euler; the tile range of the new position.
 //     The same thread then appends the particle to the tile lists of its new
@@ -15,10 +15,13 @@
 
 namespace vlb {
 
-__device__ __forceinline__ int4 tile_range(const ParticleConst& c, double X, double Y, double R) {
-  const double m = c.margin;
-  int cx0 = (int)floor(X - R - m), cx1 = (int)floor(X + R + m);
-  int cy0 = (int)floor(Y - R - m), cy1 = (int)floor(Y + R + m);
+// Tiles covered by [X - R - m, X + R + m] (clipped to the domain), in FP32: the
+// margin m >= 2 cells absorbs the rounding, and the range is computed once per
+// step and stored, so every use of it agrees.
+__device__ __forceinline__ int4 tile_range(const ParticleConst& c, double Xd, double Yd, double Rd) {
+  const float X = float(Xd), Y = float(Yd), e = float(Rd) + float(c.margin);
+  int cx0 = (int)floorf(X - e), cx1 = (int)floorf(X + e);
+  int cy0 = (int)floorf(Y - e), cy1 = (int)floorf(Y + e);
   cx0 = max(cx0, 0); cy0 = max(cy0, 0);
   cx1 = min(cx1, c.nx - 1); cy1 = min(cy1, c.ny - 1);
   if (cx1 < cx0 || cy1 < cy0) return make_int4(0, 0, 0, 0);
@@ -35,84 +38,150 @@ __device__ __forceinline__ void check_domain(const ParticleConst& c, double X, d
   if (bad) atomicOr(err, ERR_OUT_OF_DOMAIN);
 }
 
+// Raster record of particle p at centre (X, Y) with velocity (ux, uy, om).
+__device__ __forceinline__ void write_record(const ParticleArrays& P, int p, double X, double Y, double R,
+                                             double ux, double uy, double om, float lam_s, float T0) {
+  RasterRec q;
+  const double Q = double(1 << QBITS);
+  q.xi = (int)floor(X);
+  q.yi = (int)floor(Y);
+  q.qfx = (int)(__double2ll_rn(X * Q) - (long long)q.xi * (1ll << QBITS));
+  q.qfy = (int)(__double2ll_rn(Y * Q) - (long long)q.yi * (1ll << QBITS));
+  const long long rq = __double2ll_rn(R * Q);
+  q.rq2 = rq * rq;
+  const double fx = X - double(q.xi), fy = Y - double(q.yi);
+  q.xfh = float(fx); q.xfl = float(fx - double(q.xfh));
+  q.yfh = float(fy); q.yfl = float(fy - double(q.yfh));
+  q.r = float(R);
+  q.far2 = float((R + 0.75) * (R + 0.75));
+  q.near2 = R > 0.75 ? float((R - 0.75) * (R - 0.75)) : -1.0f;
+  q.ux = float(ux); q.uxl = float(ux - double(q.ux));
+  q.uy = float(uy); q.uyl = float(uy - double(q.uy));
+  q.om = float(om);
+  q.lam_s = lam_s;
+  q.T0 = T0;
+  P.rec[p] = q;
+}
+
 __global__ void particle_range_kernel(const ParticleConst c, const ParticleArrays P, unsigned* err) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.np) return;
   const int4 rg = tile_range(c, P.x[p], P.y[p], P.r[p]);
   if (rg.z * rg.w > c.kt) atomicOr(err, ERR_PARTIAL_OVERFLOW);
   P.prange[p] = rg;
+  write_record(P, p, P.x[p], P.y[p], P.r[p], P.ux[p], P.uy[p], P.om[p], float(P.lam_s[p]), float(P.T0[p]));
 }
 
+// Append particle p to the lists of the tiles of range rg.  The atomics are
+// issued in batches of 8 so that their round trips overlap.
 __device__ __forceinline__ void bin_particle(const ParticleConst& c, const TileLists& TL, int p, int4 rg,
                                              unsigned* err) {
-  for (int b = 0; b < rg.w; ++b)
-    for (int a = 0; a < rg.z; ++a) {
-      const int t = (rg.y + b) * c.ntx + (rg.x + a);
-      const int slot = atomicAdd(&TL.count[t], 1);
-      if (slot < TILE_CAP) TL.ids[(long long)t * TILE_CAP + slot] = p;
+  const int n = rg.z * rg.w;
+  for (int t0 = 0; t0 < n; t0 += 8) {
+    int tile[8], slot[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u;
+      tile[u] = t < n ? (rg.y + t / rg.z) * c.ntx + (rg.x + t % rg.z) : -1;
+      slot[u] = tile[u] >= 0 ? atomicAdd(&TL.count[tile[u]], 1) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (tile[u] < 0) continue;
+      if (slot[u] < TILE_CAP) TL.ids[(long long)tile[u] * TILE_CAP + slot[u]] = p;
       else atomicOr(err, ERR_TILE_OVERFLOW);
     }
+  }
 }
 
+// One thread per particle: each FP64 instruction then serves 32 particles
+// (GB300's FP64 pipe is narrow, so this layout matters more than latency).
 __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArrays P, const TileLists TL,
                                         unsigned* err) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.np) return;
   const double X = P.x[p], Y = P.y[p], R = P.r[p];
-  // momentum-exchange force and torque of the current level (Eq. 28)
+  const double ux = P.ux[p], uy = P.uy[p], om = P.om[p];
+  const double* kp = P.pk + 8 * p;  // 1/M, 1/I, M_in, I_in, body factor, wall factor
+  double k[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) k[i] = kp[i];
+  const double ux_prev = P.ux_prev[p], uy_prev = P.uy_prev[p], om_prev = P.om_prev[p];
+  const double theta = P.theta[p];
+  const float lam_s = float(P.lam_s[p]), T0 = float(P.T0[p]);
+  // momentum-exchange force and torque of the current level (Eq. 28), summed
+  // over the tile partials in a fixed order
+  // (the loads of each batch of 4 slots, and of the first batch of partners,
+  // do not wait for the counts: they stay inside this particle's slots)
   const int4 rg = P.prange[p];
-  int nk = rg.z * rg.w;
-  if (nk > c.kt) nk = c.kt;
+  const int ncount = P.nbr_count[p];
   double Fm_x = 0.0, Fm_y = 0.0, Tm = 0.0;
   const double* part = P.partial + (long long)p * c.kt * 3;
-  for (int k = 0; k < nk; ++k) {
-    Fm_x += part[3 * k + 0];
-    Fm_y += part[3 * k + 1];
-    Tm += part[3 * k + 2];
+  for (int i0 = 0; i0 < c.kt; i0 += 4) {
+    double v[12];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[3 * u + d] = (i0 + u < c.kt) ? part[3 * (i0 + u) + d] : 0.0;
+    const int nk = min(rg.z * rg.w, c.kt);
+    if (i0 >= nk) break;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u < nk) { Fm_x += v[3 * u]; Fm_y += v[3 * u + 1]; Tm += v[3 * u + 2]; }
   }
   // contact force: partner forces (computed at this level by the lattice
   // kernel) summed in ascending partner id, then walls x-, x+, y-, y+
   double Fc_x = 0.0, Fc_y = 0.0;
-  const int nn = min(P.nbr_count[p], NBR_CAP);
-  int nb[NBR_CAP];
-  double nfx[NBR_CAP], nfy[NBR_CAP];
-  for (int a = 0; a < nn; ++a) {
-    const int j = P.nbr[p * NBR_CAP + a];
-    const double fx = P.nbr_f[2 * (p * NBR_CAP + a)], fy = P.nbr_f[2 * (p * NBR_CAP + a) + 1];
-    int k = a;
-    while (k > 0 && nb[k - 1] > j) { nb[k] = nb[k - 1]; nfx[k] = nfx[k - 1]; nfy[k] = nfy[k - 1]; --k; }
-    nb[k] = j; nfx[k] = fx; nfy[k] = fy;
-  }
-  P.nbr_count[p] = 0;  // the lattice kernel of this step lists the next partners
-  for (int a = 0; a < nn; ++a) {
-    Fc_x += nfx[a];
-    Fc_y += nfy[a];
+  {
+    int nb[NBR_CAP];
+    double nfx[NBR_CAP], nfy[NBR_CAP];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      nb[a] = P.nbr[p * NBR_CAP + a];
+      nfx[a] = P.nbr_f[2 * (p * NBR_CAP + a)];
+      nfy[a] = P.nbr_f[2 * (p * NBR_CAP + a) + 1];
+    }
+    const int nn = min(ncount, NBR_CAP);
+    for (int a = 4; a < nn; ++a) {
+      nb[a] = P.nbr[p * NBR_CAP + a];
+      nfx[a] = P.nbr_f[2 * (p * NBR_CAP + a)];
+      nfy[a] = P.nbr_f[2 * (p * NBR_CAP + a) + 1];
+    }
+    if (nn > 0) {
+      // insertion sort by partner id
+      for (int a = 1; a < nn; ++a) {
+        const int j = nb[a];
+        const double fx = nfx[a], fy = nfy[a];
+        int q = a;
+        while (q > 0 && nb[q - 1] > j) { nb[q] = nb[q - 1]; nfx[q] = nfx[q - 1]; nfy[q] = nfy[q - 1]; --q; }
+        nb[q] = j; nfx[q] = fx; nfy[q] = fy;
+      }
+      P.nbr_count[p] = 0;  // the lattice kernel of this step lists the next partners
+      for (int a = 0; a < nn; ++a) {
+        Fc_x += nfx[a];
+        Fc_y += nfy[a];
+      }
+    }
   }
   {
-    const double cw = c.contact_scale * R * R / c.eps_w;
     const double dist[4] = {X, double(c.nx) - X, Y, double(c.ny) - Y};
     const double nxw[4] = {1.0, -1.0, 0.0, 0.0}, nyw[4] = {0.0, 0.0, 1.0, -1.0};
     for (int w = 0; w < 4; ++w) {
       if ((w < 2 && c.per_x) || (w >= 2 && c.per_y)) continue;
       const double gap = 2.0 * R + c.zeta - 2.0 * dist[w];
       if (gap <= 0.0) continue;
-      const double mag = cw * (gap / c.zeta) * (gap / c.zeta);
+      const double gz = gap * c.inv_zeta;
+      const double mag = k[5] * gz * gz;
       Fc_x += mag * nxw[w];
       Fc_y += mag * nyw[w];
     }
   }
   // Eqs. 26, 29, 30: F_c = F_MES - F_in + (rho_s - rho_f) V g + F_contact
-  const double pi = 3.141592653589793;
-  const double area = pi * R * R;
-  const double M = c.rho_ratio * area, I = 0.5 * M * R * R;
-  const double Min = area, Iin = 0.5 * Min * R * R;
-  const double ux = P.ux[p], uy = P.uy[p], om = P.om[p];
-  const double Fin_x = -Min * (ux - P.ux_prev[p]);
-  const double Fin_y = -Min * (uy - P.uy_prev[p]);
-  const double Tin = -Iin * (om - P.om_prev[p]);
-  const double body = (c.rho_ratio - 1.0) * area;
-  const double Fx = Fm_x - Fin_x + body * c.gx + Fc_x;
-  const double Fy = Fm_y - Fin_y + body * c.gy + Fc_y;
+  const double Fin_x = -k[2] * (ux - ux_prev);
+  const double Fin_y = -k[2] * (uy - uy_prev);
+  const double Tin = -k[3] * (om - om_prev);
+  const double Fx = Fm_x - Fin_x + k[4] * c.gx + Fc_x;
+  const double Fy = Fm_y - Fin_y + k[4] * c.gy + Fc_y;
   const double Tc = Tm - Tin;
   P.fcx[p] = Fx;
   P.fcy[p] = Fy;
@@ -120,16 +189,18 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   const double Xn = X + ux, Yn = Y + uy;
   P.x[p] = Xn;
   P.y[p] = Yn;
-  P.theta[p] = P.theta[p] + om;
+  P.theta[p] = theta + om;
   P.ux_prev[p] = ux;
   P.uy_prev[p] = uy;
   P.om_prev[p] = om;
-  const double uxn = ux + Fx / M, uyn = uy + Fy / M;
+  const double uxn = ux + Fx * k[0], uyn = uy + Fy * k[0];
+  const double omn = om + Tc * k[1];
   P.ux[p] = uxn;
   P.uy[p] = uyn;
-  P.om[p] = om + Tc / I;
+  P.om[p] = omn;
   if (!(uxn * uxn + uyn * uyn <= 0.25)) atomicOr(err, ERR_TOO_FAST);
   check_domain(c, Xn, Yn, R, err);
+  write_record(P, p, Xn, Yn, R, uxn, uyn, omn, lam_s, T0);
   const int4 nr = tile_range(c, Xn, Yn, R);
   if (nr.z * nr.w > c.kt) atomicOr(err, ERR_PARTIAL_OVERFLOW);
   P.prange[p] = nr;
@@ -154,7 +225,7 @@ cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& 
 cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
                                     unsigned* err, cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
-  particle_advance_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, TL, err);
+  particle_advance_kernel<<<(unsigned)((c.np + 31) / 32), 32, 0, st>>>(c, P, TL, err);
   return cudaGetLastError();
 }
 cudaError_t launch_particle_bin(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,

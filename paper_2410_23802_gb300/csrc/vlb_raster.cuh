@@ -85,9 +85,14 @@ __host__ __device__ __forceinline__ float segment_area(float L, float R) {
 // point on one or the other side of a corner, the link's chord is just tiny
 // and so is its segment.
 template <class C>
-__host__ __device__ C disk_unit_cell_area(C cx, C cy, C R) {
-  C px[8], py[8];
-  int n = 0;
+__host__ __device__ __forceinline__ C disk_unit_cell_area(C cx, C cy, C R) {
+  // The polygon's points are visited in walking order (a_0, b_0, a_1, b_1, ...)
+  // and its shoelace terms and link segments summed on the fly, in that order,
+  // so no point list is kept.
+  C x0 = C(0), y0 = C(0);  // first point (a_0)
+  C xp = C(0), yp = C(0);  // last point so far
+  bool any = false;
+  C twice = C(0), seg = C(0);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     // edge 0: y = 0, x 0 -> 1; edge 1: x = 1, y 0 -> 1; edge 2: y = 1, x 1 -> 0;
@@ -105,19 +110,28 @@ __host__ __device__ C disk_unit_cell_area(C cx, C cy, C R) {
     if (!(hi > lo)) continue;
     const bool up = (k == 0 || k == 1);
     const C a = up ? lo : hi, b = up ? hi : lo;  // start and end in walking order
-    px[n] = horiz ? a : fixed; py[n] = horiz ? fixed : a; ++n;
-    px[n] = horiz ? b : fixed; py[n] = horiz ? fixed : b; ++n;
-  }
-  if (n == 0) return C(0);
-  C twice = C(0), seg = C(0);
-  for (int a = 0; a < n; ++a) {
-    const int b = (a + 1 == n) ? 0 : a + 1;
-    twice += px[a] * py[b] - px[b] * py[a];
-    if (a & 1) {  // end of one interval -> start of the next: an arc
-      const C lx = px[b] - px[a], ly = py[b] - py[a];
+    const C ax = horiz ? a : fixed, ay = horiz ? fixed : a;
+    const C bx = horiz ? b : fixed, by = horiz ? fixed : b;
+    if (any) {
+      // link from the previous interval's end to this start: a chord and its arc
+      twice += xp * ay - ax * yp;
+      const C lx = ax - xp, ly = ay - yp;
       const C L = vsqrt(lx * lx + ly * ly);
       if (L > C(0)) seg += segment_area(L < C(2) * R ? L : C(2) * R, R);
+    } else {
+      x0 = ax; y0 = ay;
+      any = true;
     }
+    twice += ax * by - bx * ay;
+    xp = bx; yp = by;
+  }
+  if (!any) return C(0);
+  // closing link from the last end back to the first start
+  twice += xp * y0 - x0 * yp;
+  {
+    const C lx = x0 - xp, ly = y0 - yp;
+    const C L = vsqrt(lx * lx + ly * ly);
+    if (L > C(0)) seg += segment_area(L < C(2) * R ? L : C(2) * R, R);
   }
   const C area = C(0.5) * twice + seg;
   return area < C(0) ? C(0) : (area > C(1) ? C(1) : area);
