@@ -2,12 +2,14 @@
 // the order of the kernels within a time step, and the copies to the host.
 //
 // One time step n -> n+1 on the handle's stream:
-//   particle_advance   F_c^n from the partials and contact forces of level n,
-//                      forward Euler to X^{n+1}, U^{n+1}; appends each particle
-//                      to the tile lists of X^{n+1} (list buffer b)
+//   particle_advance   F_c^n from the exchange sums and contact forces of level
+//                      n (clearing the sums), forward Euler to X^{n+1}, U^{n+1};
+//                      writes the raster records and appends each particle to
+//                      the tile lists of X^{n+1} (list buffer b)
 //   lattice (STEP)     fused pull / correction / thermal / collision pass that
-//                      writes level n+1, the partials and contact partners of
-//                      level n+1, and clears list buffer 1 - b for the next step
+//                      writes level n+1, adds the exchange sums of level n+1,
+//                      lists the contact partners of level n+1, and clears list
+//                      buffer 1 - b for the next step
 // The first step is preceded by the initial state (lattice INIT mode).
 #include <algorithm>
 #include <cstdlib>
@@ -42,7 +44,7 @@ struct vlb_handle {
   bool macros_valid = false;
   long long step = 0;
   // particles
-  int np = 0, cap = 0, kt = 0;
+  int np = 0, cap = 0;
   std::vector<double> hx, hy, hr, hT0, hk, hux, huy, hom;
   ParticleArrays P{};
   TileLists TL[2] = {};
@@ -93,7 +95,7 @@ static vlb_status device_flags(vlb_handle* h) {
   if (e & ERR_TILE_OVERFLOW) m += " tile list overflow;";
   if (e & ERR_OWNER_OVERFLOW) m += " more than 4 owners in a cell;";
   if (e & ERR_NBR_OVERFLOW) m += " contact partner overflow;";
-  if (e & ERR_PARTIAL_OVERFLOW) m += " partial slot overflow;";
+  if (e & ERR_MES_RANGE) m += " momentum-exchange sum out of fixed-point range;";
   if (e & ERR_OUT_OF_DOMAIN) m += " particle out of the domain;";
   if (e & ERR_TOO_FAST) m += " particle faster than 0.5 lu/step;";
   if (e & ERR_NAN) m += " NaN population;";
@@ -142,7 +144,6 @@ static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
     K.wall_dirichlet[w] = p.thermal_wall[w] == VLB_WALL_DIRICHLET;
     K.wall_dT[w] = C(p.wall_T[w] - p.T_fluid_init);
   }
-  K.kt = h->kt;
   K.np = h->np;
   // Eq. 5 with the rules of Sec. 3
   const double sp = 1.0 / p.tau_f;
@@ -177,7 +178,7 @@ static void free_all(vlb_handle* h) {
     if (h->TL[b].count) cudaFree(h->TL[b].count);
     if (h->TL[b].ids) cudaFree(h->TL[b].ids);
   }
-  if (h->P.partial) cudaFree(h->P.partial);
+  if (h->P.mes) cudaFree(h->P.mes);
   if (h->audit_scratch) cudaFree(h->audit_scratch);
   if (h->err_host) cudaFreeHost(h->err_host);
   if (h->err_dev) cudaFree(h->err_dev);
@@ -363,15 +364,11 @@ static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_b
 static vlb_status initialize(vlb_handle* h) {
   const vlb_params& p = h->p;
   const int n = h->np;
-  // partial slots: the largest tile range a disk can cover
-  double rmax = 0.0;
-  for (double r : h->hr) rmax = std::max(rmax, r);
   const double margin = 0.5 * p.contact_range + 2.0;
-  const int span = (int)std::ceil(2.0 * (rmax + margin)) + 2;
-  h->kt = std::max(1, ((span + TILE_X - 1) / TILE_X + 1) * ((span + TILE_Y - 1) / TILE_Y + 1));
   if (n > 0) {
-    CK(h, cudaMalloc(&h->P.partial, (size_t)n * h->kt * 3 * sizeof(double)));
-    CK(h, cudaMemsetAsync(h->P.partial, 0, (size_t)n * h->kt * 3 * sizeof(double), h->stream));
+    // exchange accumulators: zero before the first (initial) lattice pass
+    CK(h, cudaMalloc(&h->P.mes, (size_t)n * 6 * sizeof(unsigned long long)));
+    CK(h, cudaMemsetAsync(h->P.mes, 0, (size_t)n * 6 * sizeof(unsigned long long), h->stream));
     std::vector<double> lam(n);
     const double lam_f = (p.tau_f - 0.5) / 3.0 / p.prandtl;
     for (int k = 0; k < n; ++k) lam[k] = h->hk[k] * lam_f;
@@ -409,7 +406,7 @@ static vlb_status initialize(vlb_handle* h) {
 
   ParticleConst& c = h->PC;
   c.np = n; c.nx = h->nx; c.ny = h->ny; c.per_x = p.periodic[0]; c.per_y = p.periodic[1];
-  c.ntx = h->ntx; c.nty = h->nty; c.kt = h->kt;
+  c.ntx = h->ntx; c.nty = h->nty;
   c.rho_ratio = p.rho_ratio; c.gx = p.gravity[0]; c.gy = p.gravity[1];
   c.zeta = p.contact_range; c.eps_p = p.contact_eps_p; c.eps_w = p.contact_eps_w;
   c.contact_scale = std::fabs(p.rho_ratio - 1.0) * std::hypot(p.gravity[0], p.gravity[1]) * M_PI;

@@ -41,7 +41,7 @@ enum : unsigned {
   ERR_TILE_OVERFLOW = 1u,
   ERR_OWNER_OVERFLOW = 2u,
   ERR_NBR_OVERFLOW = 4u,
-  ERR_PARTIAL_OVERFLOW = 8u,
+  ERR_MES_RANGE = 8u,  // an exchange row sum beyond the fixed-point range
   ERR_OUT_OF_DOMAIN = 16u,
   ERR_TOO_FAST = 32u,
   ERR_NAN = 64u,
@@ -72,7 +72,7 @@ struct ParticleArrays {
   double *fcx, *fcy, *tc;  // F_c, T_c of the last update
   double *r, *lam_s, *T0;  // radius, lambda_s, initial temperature
   int4* prange;            // tile range (tx0, ty0, ntx, nty) at the current level
-  double* partial;         // [n][kt][3] MES partial sums per tile of the range
+  unsigned long long* mes; // [n][3][2] F_MES,x, F_MES,y, T_MES as fixed point (see mes_add)
   int* nbr_count;          // contact partners per particle
   int* nbr;                // [n][NBR_CAP], unordered (sorted where used)
   double* nbr_f;           // [n][NBR_CAP][2] contact force on the particle from that partner
@@ -96,6 +96,39 @@ __device__ __forceinline__ bool in_contact_range(double xi, double yi, double ri
   return d2 < __dmul_rn(thr, thr);
 }
 
+// Momentum-exchange sums (Eq. 28) are accumulated as integers, so that their
+// totals do not depend on the order in which tiles and rows add them: word 0
+// (signed, two's complement) counts units of 2^-40, word 1 (unsigned) units of
+// 2^-104 with its carries moved into word 0.  The FP32 kernel fills word 0
+// only: a row sum v becomes round(v 2^40), exact for |v| >= 2^-17 and within
+// 2^-41 below; the FP64 kernel keeps 104 fraction bits.  |v| < 2^21 is
+// required (a row of 32 cells with |f_s (rho u_s - j)| <= 1 and arm <= 10^4
+// stays far below); larger values set ERR_MES_RANGE and are dropped.
+constexpr double MES_SCALE_HI = 1099511627776.0;         // 2^40
+constexpr double MES_SCALE_LO = 18446744073709551616.0;  // 2^64
+__device__ __forceinline__ void mes_add(unsigned long long* w, float v, unsigned* err) {
+  const float t = v * 1099511627776.0f;  // exact (power of two)
+  if (!(fabsf(t) < 2.305843e18f)) { atomicOr(err, ERR_MES_RANGE); return; }  // 2^61
+  const long long q = __float2ll_rn(t);
+  if (q != 0) atomicAdd(w, (unsigned long long)q);
+}
+__device__ __forceinline__ void mes_add(unsigned long long* w, double v, unsigned* err) {
+  const double t = v * MES_SCALE_HI;
+  if (!(fabs(t) < 2.305843009213694e18)) { atomicOr(err, ERR_MES_RANGE); return; }
+  const double fl = floor(t);
+  const long long hi = (long long)fl;
+  const unsigned long long lo = (unsigned long long)((t - fl) * MES_SCALE_LO);
+  if (lo != 0ull) {
+    const unsigned long long old = atomicAdd(w + 1, lo);
+    if (old + lo < old) atomicAdd(w, 1ull);  // carry
+  }
+  if (hi != 0) atomicAdd(w, (unsigned long long)hi);
+}
+// The total of one accumulator pair as a double.
+__host__ __device__ __forceinline__ double mes_value(unsigned long long hi, unsigned long long lo) {
+  return (double)(long long)hi / MES_SCALE_HI + (double)lo / (MES_SCALE_HI * MES_SCALE_LO);
+}
+
 // Problem constants in the arithmetic type C of the lattice kernel.
 template <class C>
 struct LatticeConst {
@@ -103,7 +136,6 @@ struct LatticeConst {
   long long plane;         // elements per population plane
   int per_x, per_y;        // periodic axes
   int wall_dirichlet[4];   // x-, x+, y-, y+
-  int kt;                  // partial slots per particle
   int np;
   double zeta;             // contact range
   double contact_scale;    // |rho_r - 1| rho_f |g| pi

@@ -7,7 +7,7 @@ namespace vlb {
 
 // Constants of the particle kernels (Sec. 2.3 and the contact model).
 struct ParticleConst {
-  int np, nx, ny, per_x, per_y, ntx, nty, kt;
+  int np, nx, ny, per_x, per_y, ntx, nty;
   double rho_ratio, gx, gy;
   double zeta, eps_p, eps_w, contact_scale;  // scale = |rho_r - 1| rho_f |g| pi
   double margin;                             // tile-range margin around each disk (cells)

@@ -2,8 +2,8 @@
 //
 // Per cell, in registers:  pull f-bar and g-bar from the neighbours (Eqs. 3b,
 // 17b) with wall rules; f_s^{n+1} from the tile's particle list (Sec. 2);
-// volumetric correction of f (Eq. 8) and the momentum-exchange partials of
-// Eq. 28; df_s/dt (Eq. 24), c_v and lambda (Eq. 11), grad T (Eq. 23), T
+// volumetric correction of f (Eq. 8) and the momentum-exchange sums of
+// Eq. 28 (per row of the tile, added to per-particle integer accumulators); df_s/dt (Eq. 24), c_v and lambda (Eq. 11), grad T (Eq. 23), T
 // jointly with u and the buoyancy force (Eqs. 9, 25), eps and q_c (Eqs. 16,
 // 21); both MRT collisions (Eqs. 3a, 17a); stores of f-bar, g-bar and
 // S = 2 f_s + df_s/dt at level n+1.
@@ -48,11 +48,10 @@ __device__ __forceinline__ C warp_sum(C v) {
   return v;
 }
 
-// Shared memory of one tile: its particles and the per-row exchange sums.
+// Shared memory of one tile: its particles.
 template <class C>
 struct TileShared {
   PartTile<C> p[TILE_CAP];
-  C red[TILE_Y][TILE_CAP][3];
 };
 
 // Particle list of one tile, sorted by id (rank sort; ids are unique), with
@@ -106,8 +105,6 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
     }
     q.id = id;
     const int4 rg = P.prange[id];
-    const int kx = tile_x - rg.x, ky = tile_y - rg.y;
-    q.k = (kx >= 0 && ky >= 0 && kx < rg.z && ky < rg.w && ky * rg.z + kx < K.kt) ? ky * rg.z + kx : -1;
     q.rx = rg.x;
     q.ry = rg.y;
     s_p[rank] = q;
@@ -209,7 +206,7 @@ __device__ __forceinline__ void pull_direct(const LatticeConst<C>& K, const Step
 }
 
 // Everything of one time step at one cell after the pull: the tile's particle
-// list, f_s and owners, correction, thermal macroscopics, exchange partials,
+// list, f_s and owners, correction, thermal macroscopics, exchange sums,
 // both collisions and the stores.  Called by every thread of the CTA (it has
 // barriers); returns the tile's particle count.
 template <class S, class C, int MODE>
@@ -278,7 +275,7 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
     for (int k = 0; k < MAX_OWNERS; ++k) { own[k] = -1; ocls[k] = 0; ofs[k] = C(0); }
   }
 
-  // ---- flow: volumetric correction (Eq. 8) and exchange partials (Eq. 28) ---
+  // ---- flow: volumetric correction (Eq. 8) and the exchange terms (Eq. 28) ---
   // f holds deviations from w_i; rho = 1 + drho.
   // momenta as sums of differences of opposite populations: those differences
   // are exact when the two are close, which keeps j* accurate where it nearly
@@ -392,42 +389,36 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
   }
 
   if (MODE != MODE_MACROS) {
-    // ---- momentum-exchange partial sums per (tile, particle) -----------------
+    // ---- momentum-exchange sums (Eq. 28) -----------------------------------------
     // each warp (one row of the tile) reduces its cells with shuffles in a
-    // fixed order; one barrier; then the 8 row sums add up in row order
-    if (np > 0) {
-      for (int sl = 0; sl < np; ++sl) {
-        C v0 = C(0), v1 = C(0), v2 = C(0);
-        bool mine = false;
+    // fixed order and adds the row sums to the particle's integer
+    // accumulators: no barrier, and a total independent of the tile order
+    for (int sl = 0; sl < np; ++sl) {
+      C v0 = C(0), v1 = C(0), v2 = C(0);
+      bool mine = false;
 #pragma unroll
-        for (int k = 0; k < MAX_OWNERS; ++k)
-          if (own[k] == sl) {
-            // sum_i e_i f_i^eq(rho, u_s) = rho u_s; Delta F = -f_s,p (rho u_s - j*),
-            // formed as (U_hi - j*) + (U_lo + Omega x r) + drho u_s (Eq. 28)
-            const PartTile<C>& q = s_p[sl];
-            const C rx = ((C(tx) + C(0.5)) - q.xh) - q.xl, ry = ((C(ty) + C(0.5)) - q.yh) - q.yl;
-            const C rotx = -q.om * ry, roty = q.om * rx;
-            const C usx = q.ux + (q.uxl + rotx), usy = q.uy + (q.uyl + roty);
-            const C w = ofs[k];
-            v0 = -w * (((q.ux - jxs) + (q.uxl + rotx)) + drho * usx);
-            v1 = -w * (((q.uy - jys) + (q.uyl + roty)) + drho * usy);
-            v2 = rx * v1 - ry * v0;
-            mine = true;
-          }
-        if (__any_sync(0xffffffffu, mine)) {
-          v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+      for (int k = 0; k < MAX_OWNERS; ++k)
+        if (own[k] == sl) {
+          // sum_i e_i f_i^eq(rho, u_s) = rho u_s; Delta F = -f_s,p (rho u_s - j*),
+          // formed as (U_hi - j*) + (U_lo + Omega x r) + drho u_s (Eq. 28)
+          const PartTile<C>& q = s_p[sl];
+          const C rx = ((C(tx) + C(0.5)) - q.xh) - q.xl, ry = ((C(ty) + C(0.5)) - q.yh) - q.yl;
+          const C rotx = -q.om * ry, roty = q.om * rx;
+          const C usx = q.ux + (q.uxl + rotx), usy = q.uy + (q.uyl + roty);
+          const C w = ofs[k];
+          v0 = -w * (((q.ux - jxs) + (q.uxl + rotx)) + drho * usx);
+          v1 = -w * (((q.uy - jys) + (q.uyl + roty)) + drho * usy);
+          v2 = rx * v1 - ry * v0;
+          mine = true;
         }
-        if (tx == 0) { sh.red[ty][sl][0] = v0; sh.red[ty][sl][1] = v1; sh.red[ty][sl][2] = v2; }
-      }
-      __syncthreads();
-      for (int t = tid; t < 3 * np; t += TILE_X * TILE_Y) {
-        const int sl = t / 3, c = t - 3 * sl;
-        C acc = C(0);
-#pragma unroll
-        for (int w = 0; w < TILE_Y; ++w) acc += sh.red[w][sl][c];
-        const PartTile<C>& q = s_p[sl];
-        if (q.k >= 0) P.partial[((long long)q.id * K.kt + q.k) * 3 + c] = double(acc);
-        else if (c == 0) atomicOr(B.err, ERR_PARTIAL_OVERFLOW);
+      if (__any_sync(0xffffffffu, mine)) {
+        v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
+        if (tx == 0) {
+          unsigned long long* w = P.mes + 6 * (long long)s_p[sl].id;
+          mes_add(w, v0, B.err);
+          mes_add(w + 2, v1, B.err);
+          mes_add(w + 4, v2, B.err);
+        }
       }
     }
 

@@ -1,8 +1,8 @@
 // Particle kernels (Sec. 2.3), one thread per particle, FP64 throughout.
 //
-//   particle_advance (one thread per particle): F_MES, T_MES as the
-//     fixed-order sum of the per-tile partials of Eq. 28; the inside-fluid force and torque of Eq. 29 with backward
-//     differences; the short-range contact force; Eqs. 26 and 30 by forward
+//   particle_advance (one thread per particle): F_MES, T_MES of Eq. 28 from
+//     the integer accumulators the lattice kernel filled (then cleared); the
+//     inside-fluid force and torque of Eq. 29 with backward differences; the short-range contact force; Eqs. 26 and 30 by forward
 //     Euler; the tile range of the new position.
 //     The same thread then appends the particle to the tile lists of its new
 //     range (the lattice kernel sorts each list by id and finds the contact
@@ -67,7 +67,6 @@ __global__ void particle_range_kernel(const ParticleConst c, const ParticleArray
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.np) return;
   const int4 rg = tile_range(c, P.x[p], P.y[p], P.r[p]);
-  if (rg.z * rg.w > c.kt) atomicOr(err, ERR_PARTIAL_OVERFLOW);
   P.prange[p] = rg;
   write_record(P, p, P.x[p], P.y[p], P.r[p], P.ux[p], P.uy[p], P.om[p], float(P.lam_s[p]), float(P.T0[p]));
 }
@@ -109,26 +108,17 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   const double ux_prev = P.ux_prev[p], uy_prev = P.uy_prev[p], om_prev = P.om_prev[p];
   const double theta = P.theta[p];
   const float lam_s = float(P.lam_s[p]), T0 = float(P.T0[p]);
-  // momentum-exchange force and torque of the current level (Eq. 28), summed
-  // over the tile partials in a fixed order
-  // (the loads of each batch of 4 slots, and of the first batch of partners,
-  // do not wait for the counts: they stay inside this particle's slots)
-  const int4 rg = P.prange[p];
+  // momentum-exchange force and torque of the current level (Eq. 28): the
+  // lattice kernel's integer accumulators, read and cleared for the next level
   const int ncount = P.nbr_count[p];
-  double Fm_x = 0.0, Fm_y = 0.0, Tm = 0.0;
-  const double* part = P.partial + (long long)p * c.kt * 3;
-  for (int i0 = 0; i0 < c.kt; i0 += 4) {
-    double v[12];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) v[3 * u + d] = (i0 + u < c.kt) ? part[3 * (i0 + u) + d] : 0.0;
-    const int nk = min(rg.z * rg.w, c.kt);
-    if (i0 >= nk) break;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (i0 + u < nk) { Fm_x += v[3 * u]; Fm_y += v[3 * u + 1]; Tm += v[3 * u + 2]; }
-  }
+  unsigned long long* acc = P.mes + 6 * (long long)p;
+  const ulonglong2 a0 = reinterpret_cast<const ulonglong2*>(acc)[0];
+  const ulonglong2 a1 = reinterpret_cast<const ulonglong2*>(acc)[1];
+  const ulonglong2 a2 = reinterpret_cast<const ulonglong2*>(acc)[2];
+  const double Fm_x = mes_value(a0.x, a0.y), Fm_y = mes_value(a1.x, a1.y), Tm = mes_value(a2.x, a2.y);
+  reinterpret_cast<ulonglong2*>(acc)[0] = make_ulonglong2(0ull, 0ull);
+  reinterpret_cast<ulonglong2*>(acc)[1] = make_ulonglong2(0ull, 0ull);
+  reinterpret_cast<ulonglong2*>(acc)[2] = make_ulonglong2(0ull, 0ull);
   // contact force: partner forces (computed at this level by the lattice
   // kernel) summed in ascending partner id, then walls x-, x+, y-, y+
   double Fc_x = 0.0, Fc_y = 0.0;
@@ -202,7 +192,6 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   check_domain(c, Xn, Yn, R, err);
   write_record(P, p, Xn, Yn, R, uxn, uyn, omn, lam_s, T0);
   const int4 nr = tile_range(c, Xn, Yn, R);
-  if (nr.z * nr.w > c.kt) atomicOr(err, ERR_PARTIAL_OVERFLOW);
   P.prange[p] = nr;
   bin_particle(c, TL, p, nr, err);
 }

@@ -31,7 +31,7 @@ struct PartTile {
   C ux, uy, om;           // rigid-body motion (Eq. 27)
   C uxl, uyl;             // low parts of U (U = ux + uxl to FP64 accuracy)
   C lam_s, T0;
-  int id, k;              // particle id; index of this tile in its partial slots
+  int id;                 // particle id
   int rx, ry;             // first tile of the particle's range
 };
 
