@@ -162,6 +162,7 @@ static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
   K.tau_gf = C(tgf);
   K.sj_f = C(1.0 / tgf);
   K.se_f = C(p.thermal_rates_mode == 0 ? 1.0 / (0.5 + 0.25 / (tgf - 0.5)) : 1.0);
+  K.k3_cref = C(3.0 / cref);
   K.gk_f = C(-3.0 / (cref * tgf));
 }
 

@@ -97,13 +97,14 @@ __device__ __forceinline__ bool in_contact_range(double xi, double yi, double ri
 }
 
 // Momentum-exchange sums (Eq. 28) are accumulated as integers, so that their
-// totals do not depend on the order in which tiles and rows add them: word 0
-// (signed, two's complement) counts units of 2^-40, word 1 (unsigned) units of
-// 2^-104 with its carries moved into word 0.  The FP32 kernel fills word 0
-// only: a row sum v becomes round(v 2^40), exact for |v| >= 2^-17 and within
-// 2^-41 below; the FP64 kernel keeps 104 fraction bits.  |v| < 2^21 is
-// required (a row of 32 cells with |f_s (rho u_s - j)| <= 1 and arm <= 10^4
-// stays far below); larger values set ERR_MES_RANGE and are dropped.
+// totals do not depend on the order in which cells add them: word 0 (signed,
+// two's complement) counts units of 2^-40, word 1 (unsigned) units of 2^-104
+// with its carries moved into word 0.  The FP32 kernel fills word 0 only: a
+// cell's term v becomes round(v 2^40), exact for |v| >= 2^-17 and within 2^-41
+// below (over a disk's few hundred cells the rounding stays near 1e-11, far
+// under the FP32 terms' own rounding); the FP64 kernel keeps 104 fraction bits.
+// |v| < 2^21 is required (|f_s (rho u_s - j*)| <= 1 times an arm of at most
+// 10^4 stays far below); larger values set ERR_MES_RANGE and are dropped.
 constexpr double MES_SCALE_HI = 1099511627776.0;         // 2^40
 constexpr double MES_SCALE_LO = 18446744073709551616.0;  // 2^64
 __device__ __forceinline__ void mes_add(unsigned long long* w, float v, unsigned* err) {
@@ -148,6 +149,7 @@ struct LatticeConst {
   C dT_ref;                  // T_f - T_ref
   C tau_gf, sj_f, se_f, gk_f;  // thermal rates of a fluid cell (Eqs. 18, 22, 23)
   C wall_dT[4];              // T_w - T_f per side
+  C k3_cref;                 // 3 / c_ref
 };
 
 struct StepBuffers {

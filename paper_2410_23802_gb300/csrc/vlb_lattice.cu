@@ -330,10 +330,10 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
   // cells use the precomputed values)
   C tau_g = K.tau_gf, sj = K.sj_f, se = K.se_f, gk = K.gk_f;
   if (nown > 0) {
-    tau_g = C(0.5) + C(3) * lam / K.cref;
+    tau_g = C(0.5) + lam * K.k3_cref;  // 3 / c_ref
     sj = C(1) / tau_g;
     se = (K.rates_mode == C(0)) ? (tau_g - C(0.5)) / (C(0.5) * (tau_g - C(0.5)) + C(0.25)) : C(1);
-    gk = C(-3) * sj / K.cref;  // Eq. 23: -6/(4 + alpha_1) / (c_ref tau_g)
+    gk = -sj * K.k3_cref;  // Eq. 23: -6/(4 + alpha_1) / (c_ref tau_g)
   }
   C dT, deps, dG, qc, dfs, ux, uy;
   const C half_inv_rho = C(0.5) * inv_rho;
@@ -390,36 +390,25 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
 
   if (MODE != MODE_MACROS) {
     // ---- momentum-exchange sums (Eq. 28) -----------------------------------------
-    // each warp (one row of the tile) reduces its cells with shuffles in a
-    // fixed order and adds the row sums to the particle's integer
-    // accumulators: no barrier, and a total independent of the tile order
-    for (int sl = 0; sl < np; ++sl) {
-      C v0 = C(0), v1 = C(0), v2 = C(0);
-      bool mine = false;
+    // every owned cell adds its terms to the particle's integer accumulators
+    // (no reduction, no barrier; a total independent of the order)
 #pragma unroll
-      for (int k = 0; k < MAX_OWNERS; ++k)
-        if (own[k] == sl) {
-          // sum_i e_i f_i^eq(rho, u_s) = rho u_s; Delta F = -f_s,p (rho u_s - j*),
-          // formed as (U_hi - j*) + (U_lo + Omega x r) + drho u_s (Eq. 28)
-          const PartTile<C>& q = s_p[sl];
-          const C rx = ((C(tx) + C(0.5)) - q.xh) - q.xl, ry = ((C(ty) + C(0.5)) - q.yh) - q.yl;
-          const C rotx = -q.om * ry, roty = q.om * rx;
-          const C usx = q.ux + (q.uxl + rotx), usy = q.uy + (q.uyl + roty);
-          const C w = ofs[k];
-          v0 = -w * (((q.ux - jxs) + (q.uxl + rotx)) + drho * usx);
-          v1 = -w * (((q.uy - jys) + (q.uyl + roty)) + drho * usy);
-          v2 = rx * v1 - ry * v0;
-          mine = true;
-        }
-      if (__any_sync(0xffffffffu, mine)) {
-        v0 = warp_sum(v0); v1 = warp_sum(v1); v2 = warp_sum(v2);
-        if (tx == 0) {
-          unsigned long long* w = P.mes + 6 * (long long)s_p[sl].id;
-          mes_add(w, v0, B.err);
-          mes_add(w + 2, v1, B.err);
-          mes_add(w + 4, v2, B.err);
-        }
-      }
+    for (int k = 0; k < MAX_OWNERS; ++k) {
+      if (k >= nown) break;
+      // sum_i e_i f_i^eq(rho, u_s) = rho u_s; Delta F = -f_s,p (rho u_s - j*),
+      // formed as (U_hi - j*) + (U_lo + Omega x r) + drho u_s (Eq. 28)
+      const PartTile<C>& q = s_p[own[k]];
+      const C rx = ((C(tx) + C(0.5)) - q.xh) - q.xl, ry = ((C(ty) + C(0.5)) - q.yh) - q.yl;
+      const C rotx = -q.om * ry, roty = q.om * rx;
+      const C usx = q.ux + (q.uxl + rotx), usy = q.uy + (q.uyl + roty);
+      const C w = ofs[k];
+      const C v0 = -w * (((q.ux - jxs) + (q.uxl + rotx)) + drho * usx);
+      const C v1 = -w * (((q.uy - jys) + (q.uyl + roty)) + drho * usy);
+      const C v2 = rx * v1 - ry * v0;
+      unsigned long long* acc = P.mes + 6 * (long long)q.id;
+      mes_add(acc, v0, B.err);
+      mes_add(acc + 2, v1, B.err);
+      mes_add(acc + 4, v2, B.err);
     }
 
     if (!active) return np;
