@@ -95,6 +95,7 @@ static vlb_status device_flags(vlb_handle* h) {
   if (e & ERR_TILE_OVERFLOW) m += " tile list overflow;";
   if (e & ERR_OWNER_OVERFLOW) m += " more than 4 owners in a cell;";
   if (e & ERR_NBR_OVERFLOW) m += " contact partner overflow;";
+  if (e & ERR_BAND) m += " band table entry of another level;";
   if (e & ERR_MES_RANGE) m += " momentum-exchange sum out of fixed-point range;";
   if (e & ERR_OUT_OF_DOMAIN) m += " particle out of the domain;";
   if (e & ERR_TOO_FAST) m += " particle faster than 0.5 lu/step;";
@@ -180,6 +181,7 @@ static void free_all(vlb_handle* h) {
     if (h->TL[b].ids) cudaFree(h->TL[b].ids);
   }
   if (h->P.mes) cudaFree(h->P.mes);
+  if (h->P.band) cudaFree(h->P.band);
   if (h->audit_scratch) cudaFree(h->audit_scratch);
   if (h->err_host) cudaFreeHost(h->err_host);
   if (h->err_dev) cudaFree(h->err_dev);
@@ -362,14 +364,32 @@ static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_b
   return VLB_OK;
 }
 
+// Each band-kernel pass writes its entries with a new stamp (1 .. 2^29 - 1,
+// cycling); the lattice and dump kernels accept only entries with the stamp of
+// the tables they are given.
+static void next_band_stamp(vlb_handle* h) {
+  int s = h->PC.band_stamp + 1;
+  if (s >= (1 << 29)) s = 1;
+  h->PC.band_stamp = s;
+  h->K32.band_stamp = h->K64.band_stamp = s;
+}
+
 static vlb_status initialize(vlb_handle* h) {
   const vlb_params& p = h->p;
   const int n = h->np;
   const double margin = 0.5 * p.contact_range + 2.0;
+  // band tables: a box of 2 band_off + 1 cells around each disk's centre cell
+  // holds every cell with |d - R| < 0.75 (the centre lies in [xi, xi + 1))
+  double rmax = 0.0;
+  for (double r : h->hr) rmax = std::max(rmax, r);
+  const int band_off = (int)std::ceil(rmax) + 2;
   if (n > 0) {
     // exchange accumulators: zero before the first (initial) lattice pass
     CK(h, cudaMalloc(&h->P.mes, (size_t)n * 6 * sizeof(unsigned long long)));
     CK(h, cudaMemsetAsync(h->P.mes, 0, (size_t)n * 6 * sizeof(unsigned long long), h->stream));
+    const size_t bw = 2 * (size_t)band_off + 1;
+    CK(h, cudaMalloc(&h->P.band, (size_t)n * bw * bw * sizeof(int2)));
+    CK(h, cudaMemsetAsync(h->P.band, 0, (size_t)n * bw * bw * sizeof(int2), h->stream));
     std::vector<double> lam(n);
     const double lam_f = (p.tau_f - 0.5) / 3.0 / p.prandtl;
     for (int k = 0; k < n; ++k) lam[k] = h->hk[k] * lam_f;
@@ -408,6 +428,9 @@ static vlb_status initialize(vlb_handle* h) {
   ParticleConst& c = h->PC;
   c.np = n; c.nx = h->nx; c.ny = h->ny; c.per_x = p.periodic[0]; c.per_y = p.periodic[1];
   c.ntx = h->ntx; c.nty = h->nty;
+  c.band_off = band_off;
+  c.inv_band_w = 1.0f / float(2 * band_off + 1);
+  h->K32.band_off = h->K64.band_off = band_off;
   c.rho_ratio = p.rho_ratio; c.gx = p.gravity[0]; c.gy = p.gravity[1];
   c.zeta = p.contact_range; c.eps_p = p.contact_eps_p; c.eps_w = p.contact_eps_w;
   c.contact_scale = std::fabs(p.rho_ratio - 1.0) * std::hypot(p.gravity[0], p.gravity[1]) * M_PI;
@@ -419,6 +442,8 @@ static vlb_status initialize(vlb_handle* h) {
   CK(h, launch_particle_range(c, h->P, h->err_dev, h->stream));
   h->tl = 0;
   CK(h, launch_particle_bin(c, h->P, h->TL[0], h->err_dev, h->stream));
+  next_band_stamp(h);
+  CK(h, launch_particle_band(c, h->P, h->stream));
   h->cur = 0;
   vlb_status s = launch_lattice(h, MODE_INIT, 0, 0, 0);
   if (s != VLB_OK) return s;
@@ -437,6 +462,8 @@ vlb_status vlb_step(vlb_handle* h, int32_t nsteps) {
   for (int k = 0; k < nsteps; ++k) {
     const int nl = 1 - h->tl;
     CK(h, launch_particle_advance(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
+    next_band_stamp(h);
+    CK(h, launch_particle_band(h->PC, h->P, h->stream));
     const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
     if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
     if ((s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur, nl)) != VLB_OK) return s;
@@ -654,7 +681,7 @@ vlb_status vlb_profile_end(vlb_handle* h, double* lattice_ms, int32_t* lattice_l
   if (lattice_ms) *lattice_ms = tot;
   if (lattice_launches) *lattice_launches = h->ev_used / 2;
   // particle_advance (with binning) and the lattice kernel
-  if (launches_per_step) *launches_per_step = h->np > 0 ? 2 : 1;
+  if (launches_per_step) *launches_per_step = h->np > 0 ? 3 : 1;
   h->prof = false;
   h->ev_used = 0;
   return VLB_OK;

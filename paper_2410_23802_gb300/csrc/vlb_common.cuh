@@ -45,6 +45,7 @@ enum : unsigned {
   ERR_OUT_OF_DOMAIN = 16u,
   ERR_TOO_FAST = 32u,
   ERR_NAN = 64u,
+  ERR_BAND = 128u,  // a band cell whose table entry is not of the current level
 };
 
 // Kernel modes of the lattice kernel.
@@ -78,6 +79,8 @@ struct ParticleArrays {
   double* nbr_f;           // [n][NBR_CAP][2] contact force on the particle from that partner
   double* pk;              // [n][8] constants: 1/M, 1/I, M_in, I_in, body force factor, wall factor
   RasterRec* rec;          // [n] raster records of the current level
+  int2* band;              // [n][bw][bw] band tables: (class | stamp << 2, area bits) of the cells of
+                           // each disk's box, bw = 2 band_off + 1, centred on the record's cell
 };
 
 struct TileLists {
@@ -136,6 +139,8 @@ struct LatticeConst {
   int nx, ny, pitch, ntx, nty;
   long long plane;         // elements per population plane
   int per_x, per_y;        // periodic axes
+  int band_off;            // half-width of the band tables (cells)
+  int band_stamp;          // level stamp the band tables must carry
   int wall_dirichlet[4];   // x-, x+, y-, y+
   int np;
   double zeta;             // contact range

@@ -8,6 +8,9 @@ namespace vlb {
 // Constants of the particle kernels (Sec. 2.3 and the contact model).
 struct ParticleConst {
   int np, nx, ny, per_x, per_y, ntx, nty;
+  int band_off;      // half-width of the band tables (cells)
+  int band_stamp;    // level stamp written into the band tables
+  float inv_band_w;  // 1 / (2 band_off + 1)
   double rho_ratio, gx, gy;
   double zeta, eps_p, eps_w, contact_scale;  // scale = |rho_r - 1| rho_f |g| pi
   double margin;                             // tile-range margin around each disk (cells)
@@ -35,6 +38,7 @@ cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& 
                                   cudaStream_t st);
 cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
                                     unsigned* err, cudaStream_t st);
+cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, cudaStream_t st);
 cudaError_t launch_particle_bin(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
                                 unsigned* err, cudaStream_t st);
 

@@ -74,19 +74,13 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
     int rank = 0;
     for (int k = 0; k < np; ++k) rank += ids[k] < id;
     PartTile<C> q;
-    if (sizeof(C) == 4) {
+    if constexpr (sizeof(C) == 4) {
       // FP32 kernel: the particle kernel's raster record, no FP64 arithmetic
+      // (the geometry the band kernel used for this tile)
       const RasterRec rc = P.rec[id];
-      const long long Q = 1ll << QBITS;
-      q.xq = (long long)(rc.xi - x0) * Q + rc.qfx;
-      q.yq = (long long)(rc.yi - y0) * Q + rc.qfy;
-      q.rq2 = rc.rq2;
-      const C fx = C(rc.xi - x0), fy = C(rc.yi - y0);  // exact small integers
-      q.xh = fx + C(rc.xfh); q.xl = ((fx - q.xh) + C(rc.xfh)) + C(rc.xfl);
-      q.yh = fy + C(rc.yfh); q.yl = ((fy - q.yh) + C(rc.yfh)) + C(rc.yfl);
-      q.r = C(rc.r); q.far2 = C(rc.far2); q.near2 = C(rc.near2);
-      q.ux = C(rc.ux); q.uxl = C(rc.uxl); q.uy = C(rc.uy); q.uyl = C(rc.uyl); q.om = C(rc.om);
-      q.lam_s = C(rc.lam_s); q.T0 = C(rc.T0);
+      tile_geometry(rc, x0, y0, q);
+      q.ux = rc.ux; q.uxl = rc.uxl; q.uy = rc.uy; q.uyl = rc.uyl; q.om = rc.om;
+      q.lam_s = rc.lam_s; q.T0 = rc.T0;
     } else {
       const double X = P.x[id] - double(x0), Y = P.y[id] - double(y0), R = P.r[id];
       const long long Q = 1ll << QBITS;
@@ -102,6 +96,7 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
       q.ux = C(P.ux[id]); q.uy = C(P.uy[id]); q.om = C(P.om[id]);
       q.uxl = C(P.ux[id] - double(q.ux)); q.uyl = C(P.uy[id] - double(q.uy));
       q.lam_s = C(P.lam_s[id]); q.T0 = C(P.T0[id]);
+      q.ci = 0; q.cj = 0;
     }
     q.id = id;
     const int4 rg = P.prange[id];
@@ -114,18 +109,45 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
 }
 
 // Owners of cell (tx, ty) of the tile: ascending particle order, at most
-// MAX_OWNERS, fractions scaled to sum 1 when they exceed it (overlap).
+// MAX_OWNERS, fractions scaled to sum 1 when they exceed it (overlap).  The
+// FP32 kernel reads the exact class and area of band cells from the band
+// tables (gx, gy: the cell's lattice coordinates), which must carry the
+// level's stamp; the FP64 kernel computes them here.
 template <class C>
-__device__ __forceinline__ C raster_cell(int tx, int ty, int np, const PartTile<C>* s_p, int& nown,
-                                         int (&own)[MAX_OWNERS], int (&cls)[MAX_OWNERS],
+__device__ __forceinline__ C raster_cell(int tx, int ty, int gx, int gy, int np, const PartTile<C>* s_p,
+                                         const int2* __restrict__ band, int band_off, int band_stamp,
+                                         int& nown, int (&own)[MAX_OWNERS], int (&cls)[MAX_OWNERS],
                                          C (&ofs)[MAX_OWNERS], unsigned* err) {
   nown = 0;
 #pragma unroll
   for (int k = 0; k < MAX_OWNERS; ++k) { own[k] = -1; cls[k] = 0; ofs[k] = C(0); }
   for (int s = 0; s < np; ++s) {
     C f;
-    const int c = cell_fraction(tx, ty, s_p[s], f);
-    if (c == CELL_FLUID) continue;
+    int c;
+    if constexpr (sizeof(C) == 4) {
+      const PartTile<C>& q = s_p[s];
+      c = quick_class(tx, ty, q);
+      if (c == CELL_FLUID) continue;
+      if (c == CELL_SOLID) {
+        f = C(1);
+      } else {
+        const int bw = 2 * band_off + 1;
+        const int bx = gx - q.ci + band_off, by = gy - q.cj + band_off;
+        int2 e = make_int2(0, 0);
+        if ((unsigned)bx < (unsigned)bw && (unsigned)by < (unsigned)bw)
+          e = band[((long long)q.id * bw + by) * bw + bx];
+        if ((e.x >> 2) != band_stamp) {  // not written for this level (cannot happen)
+          atomicOr(err, ERR_BAND);
+          continue;
+        }
+        c = e.x & 3;
+        f = __int_as_float(e.y);
+        if (c == CELL_FLUID) continue;
+      }
+    } else {
+      c = cell_fraction(tx, ty, s_p[s], f);
+      if (c == CELL_FLUID) continue;
+    }
     if (nown == MAX_OWNERS) { atomicOr(err, ERR_OWNER_OVERFLOW); break; }
 #pragma unroll
     for (int k = 0; k < MAX_OWNERS; ++k)
@@ -269,7 +291,8 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
   int own[MAX_OWNERS], ocls[MAX_OWNERS];
   C ofs[MAX_OWNERS];
   C fs = C(0);
-  if (active && np > 0) fs = raster_cell<C>(tx, ty, np, s_p, nown, own, ocls, ofs, B.err);
+  if (active && np > 0)
+    fs = raster_cell<C>(tx, ty, x, y, np, s_p, P.band, K.band_off, K.band_stamp, nown, own, ocls, ofs, B.err);
   else {
 #pragma unroll
     for (int k = 0; k < MAX_OWNERS; ++k) { own[k] = -1; ocls[k] = 0; ofs[k] = C(0); }
@@ -531,7 +554,7 @@ raster_dump_kernel(const LatticeConst<C> K, const ParticleArrays P, const TileLi
   int nown, own[MAX_OWNERS], cls[MAX_OWNERS];
   C ofs[MAX_OWNERS];
   const PartTile<C>* s_p = sh.p;
-  raster_cell<C>(tx, ty, np, s_p, nown, own, cls, ofs, err);
+  raster_cell<C>(tx, ty, x, y, np, s_p, P.band, K.band_off, K.band_stamp, nown, own, cls, ofs, err);
   const long long c = (long long)y * K.nx + x;
   count[c] = (unsigned char)nown;
 #pragma unroll

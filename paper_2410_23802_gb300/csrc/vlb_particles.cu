@@ -12,6 +12,7 @@
 
 #include "vlb_common.cuh"
 #include "vlb_kernels.h"
+#include "vlb_raster.cuh"
 
 namespace vlb {
 
@@ -203,6 +204,68 @@ __global__ void particle_bin_kernel(const ParticleConst c, const ParticleArrays 
   bin_particle(c, TL, p, P.prange[p], err);
 }
 
+// Exact classes and areas (Sec. 2) of the cells whose centre lies in the band
+// |d - R| < 0.75 of a disk, i.e. the cells the lattice kernel's quick test
+// leaves open; one warp per particle.  The warp runs the quick test of each
+// cell of the disk's box (2 band_off + 1 cells square, centred on the record's
+// cell) as seen from the tile the cell lies in, queues the band cells, and
+// evaluates the queue 32 cells at a time, so that no lane idles through the
+// exact code.  Results go to the particle's band table with the level's
+// stamp; the geometry (tile_geometry) and the tests are the ones the lattice
+// kernel itself uses, so the results are the ones it would compute.
+constexpr int BAND_WARPS = 4;    // particles per CTA
+constexpr int BAND_QUEUE = 256;  // queued band cells per warp before an evaluation pass
+
+__device__ __forceinline__ void band_evaluate(const ParticleConst& c, const ParticleArrays& P, int p,
+                                              const RasterRec& rc, int bw, const int* queue, int nq, int lane) {
+  for (int j = lane; j < nq; j += 32) {
+    const int k = queue[j];
+    const int by = k / bw, bx = k - by * bw;
+    const int x = rc.xi - c.band_off + bx, y = rc.yi - c.band_off + by;
+    const int x0 = x - x % TILE_X, y0 = y - y % TILE_Y;
+    PartTile<float> q;
+    tile_geometry(rc, x0, y0, q);
+    float f;
+    const int cls = cell_fraction(x - x0, y - y0, q, f);
+    P.band[(long long)p * bw * bw + k] = make_int2(cls | (c.band_stamp << 2), __float_as_int(f));
+  }
+}
+
+__global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const ParticleConst c, const ParticleArrays P) {
+  __shared__ int s_queue[BAND_WARPS][BAND_QUEUE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * BAND_WARPS + warp;
+  if (p >= c.np) return;  // the whole warp
+  int* queue = s_queue[warp];
+  const RasterRec rc = P.rec[p];
+  const int bw = 2 * c.band_off + 1, ncell = bw * bw;
+  int nq = 0;
+  for (int k0 = 0; k0 < ncell; k0 += 32) {
+    const int k = k0 + lane;
+    const int by = (int)((float(k) + 0.5f) * c.inv_band_w);  // k / bw, exact for k < 2^20
+    const int bx = k - by * bw;
+    const int x = rc.xi - c.band_off + bx, y = rc.yi - c.band_off + by;
+    bool in_band = false;
+    if (k < ncell && x >= 0 && x < c.nx && y >= 0 && y < c.ny) {
+      const int x0 = x - x % TILE_X, y0 = y - y % TILE_Y;
+      PartTile<float> q;
+      tile_geometry(rc, x0, y0, q);
+      in_band = quick_class(x - x0, y - y0, q) == CELL_BAND;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in_band);
+    if (in_band) queue[nq + __popc(m & ((1u << lane) - 1u))] = k;
+    nq += __popc(m);
+    if (nq > BAND_QUEUE - 32) {  // evaluate what is queued before it can overflow
+      __syncwarp();
+      band_evaluate(c, P, p, rc, bw, queue, nq, lane);
+      __syncwarp();
+      nq = 0;
+    }
+  }
+  __syncwarp();
+  band_evaluate(c, P, p, rc, bw, queue, nq, lane);
+}
+
 static inline dim3 pgrid(int n) { return dim3((unsigned)((n + 127) / 128)); }
 
 cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& P, unsigned* err,
@@ -215,6 +278,11 @@ cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays
                                     unsigned* err, cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
   particle_advance_kernel<<<(unsigned)((c.np + 31) / 32), 32, 0, st>>>(c, P, TL, err);
+  return cudaGetLastError();
+}
+cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, cudaStream_t st) {
+  if (c.np == 0) return cudaSuccess;
+  particle_band_kernel<<<(unsigned)((c.np + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(c, P);
   return cudaGetLastError();
 }
 cudaError_t launch_particle_bin(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,

@@ -19,6 +19,37 @@ namespace vlb {
 __host__ __device__ __forceinline__ float vsqrt(float v) { return sqrtf(v); }
 __host__ __device__ __forceinline__ double vsqrt(double v) { return sqrt(v); }
 
+// Products and sums rounded one by one (no contraction into FMA), so that a
+// test gives the same answer in every kernel that makes it.
+__host__ __device__ __forceinline__ float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ float add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ double mul_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ double add_rn(double a, double b) {
+#ifdef __CUDA_ARCH__
+  return __dadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+
 enum : int { CELL_FLUID = 0, CELL_INTERFACE = 1, CELL_SOLID = 2 };
 
 // One particle as seen from one tile (shared memory).  Coordinates are
@@ -32,6 +63,7 @@ struct PartTile {
   C uxl, uyl;             // low parts of U (U = ux + uxl to FP64 accuracy)
   C lam_s, T0;
   int id;                 // particle id
+  int ci, cj;             // cell of the centre (band table origin)
   int rx, ry;             // first tile of the particle's range
 };
 
@@ -137,15 +169,28 @@ __host__ __device__ __forceinline__ C disk_unit_cell_area(C cx, C cy, C R) {
   return area < C(0) ? C(0) : (area > C(1) ? C(1) : area);
 }
 
+// Quick class of tile cell (il, jl): CELL_FLUID or CELL_SOLID where the
+// centre distance decides it, CELL_BAND where the exact test is needed.  The
+// FP32 lattice kernel and the band kernel both take this decision, so it is
+// rounded step by step (mul_rn, add_rn) to come out the same in both.
+enum : int { CELL_BAND = 3 };
+template <class C>
+__host__ __device__ __forceinline__ int quick_class(int il, int jl, const PartTile<C>& p) {
+  // centre distance from the cell centre (hi/lo sums keep FP32 exact enough)
+  const C dx = add_rn(add_rn(add_rn(C(il), C(0.5)), -p.xh), -p.xl);
+  const C dy = add_rn(add_rn(add_rn(C(jl), C(0.5)), -p.yh), -p.yl);
+  const C d2 = add_rn(mul_rn(dx, dx), mul_rn(dy, dy));
+  if (d2 >= p.far2) return CELL_FLUID;   // nearest point > R + 0.04
+  if (d2 <= p.near2) return CELL_SOLID;  // farthest corner < R - 0.04
+  return CELL_BAND;
+}
+
 // Class and solid fraction of tile cell (il, jl) for one particle.
 template <class C>
 __host__ __device__ __forceinline__ int cell_fraction(int il, int jl, const PartTile<C>& p, C& fsp) {
-  // centre distance from the cell centre (hi/lo sums keep FP32 exact enough)
-  const C dx = ((C(il) + C(0.5)) - p.xh) - p.xl;
-  const C dy = ((C(jl) + C(0.5)) - p.yh) - p.yl;
-  const C d2 = dx * dx + dy * dy;
-  if (d2 >= p.far2) { fsp = C(0); return CELL_FLUID; }   // nearest point > R + 0.04
-  if (d2 <= p.near2) { fsp = C(1); return CELL_SOLID; }  // farthest corner < R - 0.04
+  const int qc = quick_class(il, jl, p);
+  if (qc == CELL_FLUID) { fsp = C(0); return CELL_FLUID; }
+  if (qc == CELL_SOLID) { fsp = C(1); return CELL_SOLID; }
   const int cls = cell_class_exact(il, jl, p);
   if (cls == CELL_SOLID) { fsp = C(1); return cls; }
   if (cls == CELL_FLUID) { fsp = C(0); return cls; }
@@ -153,6 +198,22 @@ __host__ __device__ __forceinline__ int cell_fraction(int il, int jl, const Part
   const C cy = (p.yh - C(jl)) + p.yl;
   fsp = disk_unit_cell_area(cx, cy, p.r);
   return cls;
+}
+
+// The geometry fields of a particle's raster record as seen from the tile with
+// origin (x0, y0) (FP32, no FP64 arithmetic): everything cell_fraction reads.
+__host__ __device__ __forceinline__ void tile_geometry(const RasterRec& rc, int x0, int y0, PartTile<float>& q) {
+  const long long Q = 1ll << QBITS;
+  q.xq = (long long)(rc.xi - x0) * Q + rc.qfx;
+  q.yq = (long long)(rc.yi - y0) * Q + rc.qfy;
+  q.rq2 = rc.rq2;
+  const float fx = float(rc.xi - x0), fy = float(rc.yi - y0);  // exact small integers
+  q.xh = add_rn(fx, rc.xfh);
+  q.xl = add_rn(add_rn(add_rn(fx, -q.xh), rc.xfh), rc.xfl);
+  q.yh = add_rn(fy, rc.yfh);
+  q.yl = add_rn(add_rn(add_rn(fy, -q.yh), rc.yfh), rc.yfl);
+  q.r = rc.r; q.far2 = rc.far2; q.near2 = rc.near2;
+  q.ci = rc.xi; q.cj = rc.yi;
 }
 
 }  // namespace vlb
