@@ -429,7 +429,6 @@ static vlb_status initialize(vlb_handle* h) {
   c.np = n; c.nx = h->nx; c.ny = h->ny; c.per_x = p.periodic[0]; c.per_y = p.periodic[1];
   c.ntx = h->ntx; c.nty = h->nty;
   c.band_off = band_off;
-  c.inv_band_w = 1.0f / float(2 * band_off + 1);
   h->K32.band_off = h->K64.band_off = band_off;
   c.rho_ratio = p.rho_ratio; c.gx = p.gravity[0]; c.gy = p.gravity[1];
   c.zeta = p.contact_range; c.eps_p = p.contact_eps_p; c.eps_w = p.contact_eps_w;

@@ -28,9 +28,14 @@ __host__ __device__ constexpr C wgt(int i) {
   return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
 }
 
-// Tiles of the lattice kernel: one CTA of 32 x 8 threads per 32 x 8 cells.
+// Tiles of the lattice kernel: one CTA of 32 x TILE_Y threads per 32 x TILE_Y
+// cells (one warp per row of the tile).  TILE_Y is a build-time choice.
+#ifndef VLB_TILE_Y
+#define VLB_TILE_Y 8
+#endif
 constexpr int TILE_X = 32;
-constexpr int TILE_Y = 8;
+constexpr int TILE_Y = VLB_TILE_Y;
+static_assert(TILE_Y == 1 || TILE_Y == 2 || TILE_Y == 4 || TILE_Y == 8, "TILE_Y: 1, 2, 4 or 8 rows");
 constexpr int TILE_CAP = 32;   // particles listed per tile
 constexpr int MAX_OWNERS = 4;  // particles owning one cell
 constexpr int NBR_CAP = 16;    // contact partners per particle

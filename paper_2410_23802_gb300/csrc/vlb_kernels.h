@@ -10,7 +10,6 @@ struct ParticleConst {
   int np, nx, ny, per_x, per_y, ntx, nty;
   int band_off;      // half-width of the band tables (cells)
   int band_stamp;    // level stamp written into the band tables
-  float inv_band_w;  // 1 / (2 band_off + 1)
   double rho_ratio, gx, gy;
   double zeta, eps_p, eps_w, contact_scale;  // scale = |rho_r - 1| rho_f |g| pi
   double margin;                             // tile-range margin around each disk (cells)

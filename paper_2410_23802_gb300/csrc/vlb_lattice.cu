@@ -166,10 +166,10 @@ __device__ __forceinline__ C raster_cell(int tx, int ty, int gx, int gy, int np,
   return fs;
 }
 
-// CTAs per SM the FP32 register budget is sized for (4 x 256 threads: <= 64
-// registers); the FP64 variant keeps the default budget
+// CTAs per SM the FP32 register budget is sized for (1024 threads per SM:
+// <= 64 registers); the FP64 variant keeps the default budget
 #ifndef VLB_LATTICE_MIN_BLOCKS
-#define VLB_LATTICE_MIN_BLOCKS 4
+#define VLB_LATTICE_MIN_BLOCKS (1024 / (TILE_X * TILE_Y))
 #endif
 
 // Pull streaming of one cell (Eqs. 3b, 17b) with the wall rules: f-bar and

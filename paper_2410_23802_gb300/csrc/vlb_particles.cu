@@ -206,11 +206,11 @@ __global__ void particle_bin_kernel(const ParticleConst c, const ParticleArrays 
 
 // Exact classes and areas (Sec. 2) of the cells whose centre lies in the band
 // |d - R| < 0.75 of a disk, i.e. the cells the lattice kernel's quick test
-// leaves open; one warp per particle.  The warp runs the quick test of each
-// cell of the disk's box (2 band_off + 1 cells square, centred on the record's
-// cell) as seen from the tile the cell lies in, queues the band cells, and
-// evaluates the queue 32 cells at a time, so that no lane idles through the
-// exact code.  Results go to the particle's band table with the level's
+// leaves open; one warp per particle.  The warp runs the quick test of the
+// candidate cells of the disk's box (2 band_off + 1 cells square, centred on
+// the record's cell) as seen from the tile each cell lies in, queues the band
+// cells, and evaluates the queue 32 cells at a time, so that no lane idles
+// through the exact code.  Results go to the particle's band table with the level's
 // stamp; the geometry (tile_geometry) and the tests are the ones the lattice
 // kernel itself uses, so the results are the ones it would compute.
 constexpr int BAND_WARPS = 4;    // particles per CTA
@@ -238,28 +238,67 @@ __global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const Pa
   if (p >= c.np) return;  // the whole warp
   int* queue = s_queue[warp];
   const RasterRec rc = P.rec[p];
-  const int bw = 2 * c.band_off + 1, ncell = bw * bw;
+  const int bw = 2 * c.band_off + 1;
+  // Lane r takes row r of the box and only the cells of that row that can be
+  // in the band: |x - X| between sqrt((R - 0.75)^2 - dy^2) and
+  // sqrt((R + 0.75)^2 - dy^2), widened by half a cell on either side (far
+  // more than the FP32 error of these bounds).  The quick test then decides
+  // each of these candidates exactly as the lattice kernel does.
+  const float cx = float(c.band_off) + rc.xfh, cy = float(c.band_off) + rc.yfh;  // centre in box coordinates
+  const float ro = rc.r + 0.75f, ri = rc.r - 0.75f;
   int nq = 0;
-  for (int k0 = 0; k0 < ncell; k0 += 32) {
-    const int k = k0 + lane;
-    const int by = (int)((float(k) + 0.5f) * c.inv_band_w);  // k / bw, exact for k < 2^20
-    const int bx = k - by * bw;
-    const int x = rc.xi - c.band_off + bx, y = rc.yi - c.band_off + by;
-    bool in_band = false;
-    if (k < ncell && x >= 0 && x < c.nx && y >= 0 && y < c.ny) {
-      const int x0 = x - x % TILE_X, y0 = y - y % TILE_Y;
-      PartTile<float> q;
-      tile_geometry(rc, x0, y0, q);
-      in_band = quick_class(x - x0, y - y0, q) == CELL_BAND;
+  for (int by0 = 0; by0 < bw; by0 += 32) {
+    const int by = by0 + lane;
+    const int y = rc.yi - c.band_off + by;
+    int a0 = 0, a1 = -1, b0 = 0, b1 = -1;  // candidate runs [a0, a1], [b0, b1] of bx
+    if (by < bw && y >= 0 && y < c.ny) {
+      const float dy = (float(by) + 0.5f) - cy;
+      const float oa = ro * ro - dy * dy;
+      if (oa > -1.0f) {  // the row meets the widened outer circle
+        const float wa = sqrtf(fmaxf(oa, 0.0f)) + 0.5f;
+        const float ib = ri * ri - dy * dy;
+        const float wb = (ri > 0.0f && ib > 0.0f) ? sqrtf(ib) - 0.5f : 0.0f;
+        // cell bx is a candidate when |bx + 0.5 - cx| lies in [wb, wa]
+        a0 = max(0, (int)ceilf(cx - wa - 0.5f));
+        b1 = min(bw - 1, (int)floorf(cx + wa - 0.5f));
+        if (wb > 0.0f) {
+          a1 = (int)floorf(cx - wb - 0.5f);
+          b0 = (int)ceilf(cx + wb - 0.5f);
+        } else {  // one run through the middle
+          a1 = b1;
+          b0 = 0;
+          b1 = -1;
+        }
+        a1 = min(a1, bw - 1);
+        b0 = max(b0, 0);
+      }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, in_band);
-    if (in_band) queue[nq + __popc(m & ((1u << lane) - 1u))] = k;
-    nq += __popc(m);
-    if (nq > BAND_QUEUE - 32) {  // evaluate what is queued before it can overflow
-      __syncwarp();
-      band_evaluate(c, P, p, rc, bw, queue, nq, lane);
-      __syncwarp();
-      nq = 0;
+    const int na = max(a1 - a0 + 1, 0), nb = max(b1 - b0 + 1, 0);
+    int nmax = na + nb;
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    for (int j = 0; j < nmax; ++j) {
+      bool in_band = false;
+      int k = 0;
+      if (j < na + nb) {
+        const int bx = j < na ? a0 + j : b0 + (j - na);
+        const int x = rc.xi - c.band_off + bx;
+        k = by * bw + bx;
+        if (x >= 0 && x < c.nx) {
+          const int x0 = x - x % TILE_X, y0 = y - y % TILE_Y;
+          PartTile<float> q;
+          tile_geometry(rc, x0, y0, q);
+          in_band = quick_class(x - x0, y - y0, q) == CELL_BAND;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in_band);
+      if (in_band) queue[nq + __popc(m & ((1u << lane) - 1u))] = k;
+      nq += __popc(m);
+      if (nq > BAND_QUEUE - 32) {  // evaluate what is queued before it can overflow
+        __syncwarp();
+        band_evaluate(c, P, p, rc, bw, queue, nq, lane);
+        __syncwarp();
+        nq = 0;
+      }
     }
   }
   __syncwarp();
