@@ -31,7 +31,7 @@ __host__ __device__ constexpr C wgt(int i) {
 // Tiles of the lattice kernel: one CTA of 32 x TILE_Y threads per 32 x TILE_Y
 // cells (one warp per row of the tile).  TILE_Y is a build-time choice.
 #ifndef VLB_TILE_Y
-#define VLB_TILE_Y 8
+#define VLB_TILE_Y 4
 #endif
 constexpr int TILE_X = 32;
 constexpr int TILE_Y = VLB_TILE_Y;
