@@ -209,6 +209,26 @@ vlb_status vlb_get_solid_fraction_noalloc(vlb_handle* h, uint8_t* count, int32_t
  * the total number of pairs. */
 vlb_status vlb_get_contact_pairs(vlb_handle* h, int32_t capacity, int32_t* pairs, int32_t* npairs);
 
+/* Checkpoint and resume.  The state of a run after time step n (Sec. 2: the
+ * post-collision populations f-bar and g-bar, the S plane of Eq. 24, and the
+ * particle state of Sec. 2.3 with the exchange sums, contact lists and tile
+ * lists of that level) as one host image that continues the run bit for bit.
+ *   vlb_state_size: *bytes receives the image size of h (initialising h if
+ *     it has not stepped yet).
+ *   vlb_save_state: writes the image into the caller's host buffer of at
+ *     least that many bytes (synchronises the handle's stream).
+ *   vlb_load_state: restores an image into h, which must have been created
+ *     with the same parameters and given the same number of particles (their
+ *     positions and properties come from the image); afterwards vlb_step,
+ *     vlb_get_fields and the other calls continue from the saved level.
+ *     VLB_EINVAL if the image is not one of this library version or belongs
+ *     to a handle of other sizes, precision or particle count.
+ * The image holds device data of this build (storage type, tile height); it
+ * is not a portable file format. */
+vlb_status vlb_state_size(vlb_handle* h, uint64_t* bytes);
+vlb_status vlb_save_state(vlb_handle* h, void* buf, uint64_t bytes);
+vlb_status vlb_load_state(vlb_handle* h, const void* buf, uint64_t bytes);
+
 /* Measurement hooks.  Between begin and end, each step records CUDA events
  * around its lattice kernel on the handle's stream.  end() returns the summed
  * lattice-kernel time in ms, the number of timed launches, and the number of

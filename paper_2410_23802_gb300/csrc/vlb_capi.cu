@@ -50,6 +50,7 @@ struct vlb_handle {
   TileLists TL[2] = {};
   int tl = 0;  // list buffer of the current level
   void* pbase = nullptr;
+  size_t pbytes = 0;  // bytes of the particle block at pbase
   // device error word and its pinned host copy (refreshed in stream order)
   unsigned* err_host = nullptr;
   unsigned* err_dev = nullptr;
@@ -264,6 +265,7 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
                         a256(capn * NBR_CAP * 2 * sizeof(double)) + a256(capn * 8 * sizeof(double)) +
                         a256(capn * sizeof(RasterRec));
   if ((e = cudaMalloc(&h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
+  h->pbytes = pbytes;
   {
     char* b = static_cast<char*>(h->pbase);
     double** d[15] = {&h->P.x, &h->P.y, &h->P.theta, &h->P.ux, &h->P.uy, &h->P.om, &h->P.ux_prev,
@@ -649,6 +651,133 @@ vlb_status vlb_get_contact_pairs(vlb_handle* h, int32_t capacity, int32_t* pairs
     pairs[2 * k + 1] = pr[k].second;
   }
   *npairs = total;
+  return VLB_OK;
+}
+
+// ---- checkpoint and resume -------------------------------------------------
+// The image is a header followed by the device buffers that carry the state
+// of the current level, byte for byte: both population buffers and S planes
+// (the field read-back re-runs the last step's pre-collision part from the
+// previous one), the particle block (state, constants, records, ranges,
+// contact lists), the exchange accumulators, the band tables and both tile
+// list buffers.  Restoring them and the host counters continues the run
+// exactly as if it had not stopped.
+namespace {
+struct StateHeader {
+  char magic[8];
+  uint32_t version, header_bytes;
+  int32_t nx, ny, pitch, precision, storage, np, tile_y, band_off;
+  int32_t cur, tl, band_stamp, reserved;
+  int64_t step;
+  uint64_t pop_bytes, s_bytes, part_bytes, mes_bytes, band_bytes, tl_count_bytes, tl_ids_bytes;
+};
+constexpr char kStateMagic[8] = {'V', 'L', 'B', 'S', 'T', 'A', 'T', 'E'};
+
+StateHeader state_header(const vlb_handle* h) {
+  StateHeader H{};
+  std::memcpy(H.magic, kStateMagic, 8);
+  H.version = 1;
+  H.header_bytes = sizeof(StateHeader);
+  H.nx = h->nx; H.ny = h->ny; H.pitch = h->pitch; H.precision = h->p.precision; H.storage = h->storage;
+  H.np = h->np; H.tile_y = TILE_Y; H.band_off = h->PC.band_off;
+  H.cur = h->cur; H.tl = h->tl; H.band_stamp = h->PC.band_stamp;
+  H.step = h->step;
+  H.pop_bytes = (uint64_t)18 * h->plane * h->ssize;
+  H.s_bytes = (uint64_t)h->plane * h->esize;
+  H.part_bytes = h->pbytes;
+  H.mes_bytes = h->np > 0 ? (uint64_t)h->np * 6 * sizeof(unsigned long long) : 0;
+  const uint64_t bw = 2 * (uint64_t)h->PC.band_off + 1;
+  H.band_bytes = h->np > 0 ? (uint64_t)h->np * bw * bw * sizeof(int2) : 0;
+  H.tl_count_bytes = (uint64_t)h->ntx * h->nty * sizeof(int);
+  H.tl_ids_bytes = H.tl_count_bytes * TILE_CAP;
+  return H;
+}
+
+uint64_t state_bytes(const StateHeader& H) {
+  return sizeof(StateHeader) + 2 * (H.pop_bytes + H.s_bytes) + H.part_bytes + H.mes_bytes + H.band_bytes +
+         2 * (H.tl_count_bytes + H.tl_ids_bytes);
+}
+}  // namespace
+
+vlb_status vlb_state_size(vlb_handle* h, uint64_t* bytes) {
+  if (!h || !bytes) return VLB_EINVAL;
+  vlb_status s;
+  if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
+  *bytes = state_bytes(state_header(h));
+  return VLB_OK;
+}
+
+vlb_status vlb_save_state(vlb_handle* h, void* buf, uint64_t bytes) {
+  if (!h || !buf) return VLB_EINVAL;
+  vlb_status s;
+  if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
+  const StateHeader H = state_header(h);
+  if (bytes < state_bytes(H)) return fail(h, VLB_EINVAL, "vlb_save_state: buffer smaller than vlb_state_size");
+  CK(h, cudaStreamSynchronize(h->stream));
+  if ((s = device_flags(h)) != VLB_OK) return s;
+  char* o = static_cast<char*>(buf);
+  std::memcpy(o, &H, sizeof(H));
+  o += sizeof(H);
+  auto get = [&](const void* src, uint64_t n) -> cudaError_t {
+    cudaError_t e = n ? cudaMemcpy(o, src, n, cudaMemcpyDeviceToHost) : cudaSuccess;
+    o += n;
+    return e;
+  };
+  for (int b = 0; b < 2; ++b) {
+    CK(h, get(h->pop[b], H.pop_bytes));
+    CK(h, get(h->spl[b], H.s_bytes));
+  }
+  CK(h, get(h->pbase, H.part_bytes));
+  CK(h, get(h->P.mes, H.mes_bytes));
+  CK(h, get(h->P.band, H.band_bytes));
+  for (int b = 0; b < 2; ++b) {
+    CK(h, get(h->TL[b].count, H.tl_count_bytes));
+    CK(h, get(h->TL[b].ids, H.tl_ids_bytes));
+  }
+  return VLB_OK;
+}
+
+vlb_status vlb_load_state(vlb_handle* h, const void* buf, uint64_t bytes) {
+  if (!h || !buf) return VLB_EINVAL;
+  if (bytes < sizeof(StateHeader)) return fail(h, VLB_EINVAL, "vlb_load_state: buffer too small for a state image");
+  StateHeader I;
+  std::memcpy(&I, buf, sizeof(I));
+  if (std::memcmp(I.magic, kStateMagic, 8) != 0 || I.version != 1 || I.header_bytes != sizeof(StateHeader))
+    return fail(h, VLB_EINVAL, "vlb_load_state: not a state image of this library version");
+  vlb_status s;
+  if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
+  const StateHeader H = state_header(h);
+  if (I.nx != H.nx || I.ny != H.ny || I.pitch != H.pitch || I.precision != H.precision || I.storage != H.storage ||
+      I.np != H.np || I.tile_y != H.tile_y || I.band_off != H.band_off || I.pop_bytes != H.pop_bytes ||
+      I.s_bytes != H.s_bytes || I.part_bytes != H.part_bytes || I.mes_bytes != H.mes_bytes ||
+      I.band_bytes != H.band_bytes || I.tl_count_bytes != H.tl_count_bytes || I.tl_ids_bytes != H.tl_ids_bytes)
+    return fail(h, VLB_EINVAL, "vlb_load_state: the image was saved from a handle with other parameters or particles");
+  if (bytes < state_bytes(I)) return fail(h, VLB_EINVAL, "vlb_load_state: truncated state image");
+  if (I.cur < 0 || I.cur > 1 || I.tl < 0 || I.tl > 1) return fail(h, VLB_EINVAL, "vlb_load_state: corrupt header");
+  CK(h, cudaStreamSynchronize(h->stream));
+  const char* o = static_cast<const char*>(buf) + sizeof(StateHeader);
+  auto put = [&](void* dst, uint64_t n) -> cudaError_t {
+    cudaError_t e = n ? cudaMemcpy(dst, o, n, cudaMemcpyHostToDevice) : cudaSuccess;
+    o += n;
+    return e;
+  };
+  for (int b = 0; b < 2; ++b) {
+    CK(h, put(h->pop[b], I.pop_bytes));
+    CK(h, put(h->spl[b], I.s_bytes));
+  }
+  CK(h, put(h->pbase, I.part_bytes));
+  CK(h, put(h->P.mes, I.mes_bytes));
+  CK(h, put(h->P.band, I.band_bytes));
+  for (int b = 0; b < 2; ++b) {
+    CK(h, put(h->TL[b].count, I.tl_count_bytes));
+    CK(h, put(h->TL[b].ids, I.tl_ids_bytes));
+  }
+  h->cur = I.cur;
+  h->tl = I.tl;
+  h->step = I.step;
+  h->PC.band_stamp = I.band_stamp;
+  h->K32.band_stamp = h->K64.band_stamp = I.band_stamp;
+  h->macros_valid = false;
   return VLB_OK;
 }
 

@@ -87,6 +87,9 @@ def _load():
         "vlb_get_solid_fraction_noalloc": (ctypes.c_int, [h, P(ctypes.c_uint8), P(ctypes.c_int32),
                                                           P(ctypes.c_uint8), d]),
         "vlb_get_contact_pairs": (ctypes.c_int, [h, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]),
+        "vlb_state_size": (ctypes.c_int, [h, P(ctypes.c_uint64)]),
+        "vlb_save_state": (ctypes.c_int, [h, ctypes.c_void_p, ctypes.c_uint64]),
+        "vlb_load_state": (ctypes.c_int, [h, ctypes.c_void_p, ctypes.c_uint64]),
         "vlb_profile_begin": (ctypes.c_int, [h, ctypes.c_int32]),
         "vlb_profile_end": (ctypes.c_int, [h, d, P(ctypes.c_int32), P(ctypes.c_int32)]),
         "vlb_last_error": (ctypes.c_char_p, [h]),
@@ -236,6 +239,26 @@ def vlb_get_contact_pairs(h) -> np.ndarray:
     return buf[: 2 * n.value].reshape(-1, 2)
 
 
+def vlb_state_size(h) -> int:
+    n = ctypes.c_uint64()
+    _check(_lib.vlb_state_size(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def vlb_save_state(h) -> np.ndarray:
+    """The handle's state image (checkpoint) as a uint8 array."""
+    buf = np.empty(vlb_state_size(h), dtype=np.uint8)
+    _check(_lib.vlb_save_state(h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes), h)
+    return buf
+
+
+def vlb_load_state(h, image) -> None:
+    """Restore a state image (from vlb_save_state, or its bytes read back from a file)."""
+    buf = np.ascontiguousarray(np.frombuffer(image, dtype=np.uint8) if isinstance(image, (bytes, bytearray))
+                               else image, dtype=np.uint8)
+    _check(_lib.vlb_load_state(h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes), h)
+
+
 def vlb_profile_begin(h, max_steps: int):
     _check(_lib.vlb_profile_begin(h, int(max_steps)), h)
 
@@ -279,6 +302,19 @@ class Lattice:
 
     def audit(self):
         return vlb_get_audit(self.h)
+
+    def save_state(self, path=None):
+        """Checkpoint: the state image, also written to `path` if given."""
+        img = vlb_save_state(self.h)
+        if path is not None:
+            img.tofile(path)
+        return img
+
+    def load_state(self, image_or_path):
+        """Resume from a state image (array, bytes or a file written by save_state)."""
+        img = np.fromfile(image_or_path, dtype=np.uint8) if isinstance(image_or_path, (str, os.PathLike)) \
+            else image_or_path
+        vlb_load_state(self.h, img)
 
     def close(self):
         vlb_destroy(self.h)
