@@ -179,7 +179,7 @@ static void free_all(vlb_handle* h) {
   if (h->pbase) cudaFree(h->pbase);
   for (int b = 0; b < 2; ++b) {
     if (h->TL[b].count) cudaFree(h->TL[b].count);
-    if (h->TL[b].recs) cudaFree(h->TL[b].recs);
+    if (h->TL[b].ids) cudaFree(h->TL[b].ids);
   }
   if (h->P.mes) cudaFree(h->P.mes);
   if (h->P.band) cudaFree(h->P.band);
@@ -252,7 +252,7 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   const long long ntiles = (long long)h->ntx * h->nty;
   for (int b = 0; b < 2; ++b) {
     if ((e = cudaMalloc(&h->TL[b].count, ntiles * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
-    if ((e = cudaMalloc(&h->TL[b].recs, ntiles * TILE_CAP * sizeof(TileRec))) != cudaSuccess) return bail(e, "tiles");
+    if ((e = cudaMalloc(&h->TL[b].ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
     cudaMemsetAsync(h->TL[b].count, 0, ntiles * sizeof(int), h->stream);
   }
   // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints, 2 NBR_CAP + 8
@@ -689,7 +689,7 @@ StateHeader state_header(const vlb_handle* h) {
   const uint64_t bw = 2 * (uint64_t)h->PC.band_off + 1;
   H.band_bytes = h->np > 0 ? (uint64_t)h->np * bw * bw * sizeof(int2) : 0;
   H.tl_count_bytes = (uint64_t)h->ntx * h->nty * sizeof(int);
-  H.tl_ids_bytes = (uint64_t)h->ntx * h->nty * TILE_CAP * sizeof(TileRec);
+  H.tl_ids_bytes = H.tl_count_bytes * TILE_CAP;
   return H;
 }
 
@@ -732,7 +732,7 @@ vlb_status vlb_save_state(vlb_handle* h, void* buf, uint64_t bytes) {
   CK(h, get(h->P.band, H.band_bytes));
   for (int b = 0; b < 2; ++b) {
     CK(h, get(h->TL[b].count, H.tl_count_bytes));
-    CK(h, get(h->TL[b].recs, H.tl_ids_bytes));
+    CK(h, get(h->TL[b].ids, H.tl_ids_bytes));
   }
   return VLB_OK;
 }
@@ -770,7 +770,7 @@ vlb_status vlb_load_state(vlb_handle* h, const void* buf, uint64_t bytes) {
   CK(h, put(h->P.band, I.band_bytes));
   for (int b = 0; b < 2; ++b) {
     CK(h, put(h->TL[b].count, I.tl_count_bytes));
-    CK(h, put(h->TL[b].recs, I.tl_ids_bytes));
+    CK(h, put(h->TL[b].ids, I.tl_ids_bytes));
   }
   h->cur = I.cur;
   h->tl = I.tl;

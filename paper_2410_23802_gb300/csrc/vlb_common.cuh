@@ -88,17 +88,9 @@ struct ParticleArrays {
                            // each disk's box, bw = 2 band_off + 1, centred on the record's cell
 };
 
-// One entry of a tile list: the particle's raster record with its id and the
-// first tile of its range, so that the lattice kernel reads everything it
-// needs of a particle in one access.
-struct alignas(16) TileRec {
-  RasterRec rec;
-  int id, rx, ry, pad;
-};
-
 struct TileLists {
   int* count;       // [ntiles]
-  TileRec* recs;    // [ntiles][TILE_CAP], unordered
+  int* ids;         // [ntiles][TILE_CAP], unordered
   int* next_count;  // counts of the other list buffer, cleared by the lattice kernel (may be null)
 };
 

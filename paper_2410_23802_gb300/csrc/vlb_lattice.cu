@@ -68,19 +68,16 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
   const int c = TL.count[tile];
   const int np = c < TILE_CAP ? c : TILE_CAP;
   if (np == 0) return 0;
-  if (tid < 32) {  // warp 0 (np <= TILE_CAP = 32)
-    const TileRec* recs = TL.recs + (long long)tile * TILE_CAP;
-    TileRec tr;
-    if (tid < np) tr = recs[tid];
-    const int id = tid < np ? tr.id : 0x7fffffff;
-    int rank = 0;  // ids are unique: rank = number of smaller ids
-    for (int k = 0; k < np; ++k) rank += __shfl_sync(0xffffffffu, id, k) < id;
-    if (tid < np) {
+  if (tid < np) {
+    const int* ids = TL.ids + (long long)tile * TILE_CAP;
+    const int id = ids[tid];
+    int rank = 0;
+    for (int k = 0; k < np; ++k) rank += ids[k] < id;
     PartTile<C> q;
     if constexpr (sizeof(C) == 4) {
       // FP32 kernel: the particle kernel's raster record, no FP64 arithmetic
       // (the geometry the band kernel used for this tile)
-      const RasterRec& rc = tr.rec;
+      const RasterRec rc = P.rec[id];
       tile_geometry(rc, x0, y0, q);
       q.ux = rc.ux; q.uxl = rc.uxl; q.uy = rc.uy; q.uyl = rc.uyl; q.om = rc.om;
       q.lam_s = rc.lam_s; q.T0 = rc.T0;
@@ -102,10 +99,10 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
       q.ci = 0; q.cj = 0;
     }
     q.id = id;
-    q.rx = tr.rx;
-    q.ry = tr.ry;
+    const int4 rg = P.prange[id];
+    q.rx = rg.x;
+    q.ry = rg.y;
     s_p[rank] = q;
-    }
   }
   __syncthreads();
   return np;

@@ -40,8 +40,8 @@ __device__ __forceinline__ void check_domain(const ParticleConst& c, double X, d
 }
 
 // Raster record of particle p at centre (X, Y) with velocity (ux, uy, om).
-__device__ __forceinline__ RasterRec write_record(const ParticleArrays& P, int p, double X, double Y, double R,
-                                                  double ux, double uy, double om, float lam_s, float T0) {
+__device__ __forceinline__ void write_record(const ParticleArrays& P, int p, double X, double Y, double R,
+                                             double ux, double uy, double om, float lam_s, float T0) {
   RasterRec q;
   const double Q = double(1 << QBITS);
   q.xi = (int)floor(X);
@@ -62,7 +62,6 @@ __device__ __forceinline__ RasterRec write_record(const ParticleArrays& P, int p
   q.lam_s = lam_s;
   q.T0 = T0;
   P.rec[p] = q;
-  return q;
 }
 
 __global__ void particle_range_kernel(const ParticleConst c, const ParticleArrays P, unsigned* err) {
@@ -76,7 +75,7 @@ __global__ void particle_range_kernel(const ParticleConst c, const ParticleArray
 // Append particle p to the lists of the tiles of range rg.  The atomics are
 // issued in batches of 8 so that their round trips overlap.
 __device__ __forceinline__ void bin_particle(const ParticleConst& c, const TileLists& TL, int p, int4 rg,
-                                             const RasterRec& rc, unsigned* err) {
+                                             unsigned* err) {
   const int n = rg.z * rg.w;
   for (int t0 = 0; t0 < n; t0 += 8) {
     int tile[8], slot[8];
@@ -89,12 +88,7 @@ __device__ __forceinline__ void bin_particle(const ParticleConst& c, const TileL
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       if (tile[u] < 0) continue;
-      if (slot[u] < TILE_CAP) {
-        TileRec tr;
-        tr.rec = rc;
-        tr.id = p; tr.rx = rg.x; tr.ry = rg.y; tr.pad = 0;
-        TL.recs[(long long)tile[u] * TILE_CAP + slot[u]] = tr;
-      }
+      if (slot[u] < TILE_CAP) TL.ids[(long long)tile[u] * TILE_CAP + slot[u]] = p;
       else atomicOr(err, ERR_TILE_OVERFLOW);
     }
   }
@@ -197,17 +191,17 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   P.om[p] = omn;
   if (!(uxn * uxn + uyn * uyn <= 0.25)) atomicOr(err, ERR_TOO_FAST);
   check_domain(c, Xn, Yn, R, err);
-  const RasterRec rc = write_record(P, p, Xn, Yn, R, uxn, uyn, omn, lam_s, T0);
+  write_record(P, p, Xn, Yn, R, uxn, uyn, omn, lam_s, T0);
   const int4 nr = tile_range(c, Xn, Yn, R);
   P.prange[p] = nr;
-  bin_particle(c, TL, p, nr, rc, err);
+  bin_particle(c, TL, p, nr, err);
 }
 
 __global__ void particle_bin_kernel(const ParticleConst c, const ParticleArrays P, const TileLists TL,
                                     unsigned* err) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.np) return;
-  bin_particle(c, TL, p, P.prange[p], P.rec[p], err);
+  bin_particle(c, TL, p, P.prange[p], err);
 }
 
 // Exact classes and areas (Sec. 2) of the cells whose centre lies in the band
