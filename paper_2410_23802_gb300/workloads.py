@@ -112,6 +112,26 @@ def channel(precision: str = "fp64") -> Case:
     return Case("channel 100x400, 1 disk D=20", params, [50.0], [300.0], [10.0], [0.0])
 
 
+def conjugate_sedimentation(r_cv: float, length_d: float = 40.0, precision: str = "fp32") -> Case:
+    """Sedimentation of a cold disk with conjugate heat transfer in a long
+    channel (the paper's Sec. 3.4 conjugate case): D = 20 lu, width 4D, the
+    disk on the centreline, rho_r = 1.00232, Re = 10.5, Pr = 0.7, Gr = 1000,
+    tau_f = 0.53, R_lambda = 1, R_cv as given; T_c = 0 in the disk, T_h = 1 in
+    the fluid and on the walls (T_ref = T_h).  The channel length is not
+    given (length_d diameters; the disk starts 10 D below the top)."""
+    D = 20.0
+    nu = (0.53 - 0.5) / 3.0
+    u_ref = 10.5 * nu / D                                  # Re = U_ref D / nu
+    g = u_ref ** 2 / ((1.00232 - 1.0) * math.pi * D / 2.0)  # U_ref = sqrt((rho_r - 1) |g| pi D / 2)
+    nx, ny = int(4 * D), int(length_d * D)
+    params = dict(nx=nx, ny=ny, tau_f=0.53, prandtl=0.7, rho_ratio=1.00232, cv_ratio=float(r_cv),
+                  k_ratio_default=1.0, gravity=(0.0, -g), beta=gr_beta(1000.0, nu, g, 1.0, D), T_ref=1.0,
+                  T_fluid_init=1.0, thermal_wall=(1, 1, 1, 1), wall_T=(1.0, 1.0, 1.0, 1.0),
+                  thermal_rates_mode=0, precision=precision)
+    return Case(f"conjugate sedimentation {nx}x{ny}, R_cv={r_cv:g}", params, [nx / 2.0], [ny - 10.0 * D],
+                [D / 2.0], [0.0])
+
+
 def cavity(side: int = 2048, n: int = 2048, diameter: float = 16.0, seed: int = 20241031,
            precision: str = "fp32", k_log_uniform: bool = False) -> Case:
     nu = (0.8 - 0.5) / 3.0
