@@ -37,6 +37,7 @@ constexpr int TILE_X = 32;
 constexpr int TILE_Y = VLB_TILE_Y;
 static_assert(TILE_Y == 1 || TILE_Y == 2 || TILE_Y == 4 || TILE_Y == 8, "TILE_Y: 1, 2, 4 or 8 rows");
 constexpr int TILE_CAP = 32;   // particles listed per tile
+static_assert(TILE_CAP == 32, "a tile list is ranked by one warp");
 constexpr int MAX_OWNERS = 4;  // particles owning one cell
 constexpr int NBR_CAP = 16;    // contact partners per particle
 constexpr int QBITS = 20;      // fixed-point grid of the integer cell tests

@@ -65,14 +65,18 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
   const int tid = threadIdx.y * TILE_X + threadIdx.x;
   const int tile = tile_y * K.ntx + tile_x;
   const int x0 = tile_x * TILE_X, y0 = tile_y * TILE_Y;
+  // warp 0 reads the list's slots together with the count (slots beyond the
+  // count hold stale ids and are ignored), so the records wait on one load
+  int sid = 0;
+  if (tid < TILE_CAP) sid = TL.ids[(long long)tile * TILE_CAP + tid];
   const int c = TL.count[tile];
   const int np = c < TILE_CAP ? c : TILE_CAP;
   if (np == 0) return 0;
-  if (tid < np) {
-    const int* ids = TL.ids + (long long)tile * TILE_CAP;
-    const int id = ids[tid];
-    int rank = 0;
-    for (int k = 0; k < np; ++k) rank += ids[k] < id;
+  if (tid < 32) {  // warp 0 (TILE_CAP = 32): rank the ids with shuffles
+    const int id = tid < np ? sid : 0x7fffffff;
+    int rank = 0;  // ids are unique: rank = number of smaller ids
+    for (int k = 0; k < np; ++k) rank += __shfl_sync(0xffffffffu, id, k) < id;
+    if (tid < np) {
     PartTile<C> q;
     if constexpr (sizeof(C) == 4) {
       // FP32 kernel: the particle kernel's raster record, no FP64 arithmetic
@@ -103,6 +107,7 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
     q.rx = rg.x;
     q.ry = rg.y;
     s_p[rank] = q;
+    }
   }
   __syncthreads();
   return np;
