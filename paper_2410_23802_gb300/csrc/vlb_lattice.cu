@@ -342,6 +342,19 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
       cjy += w * rho * usy;
       lam += w * q.lam_s;
       dT_init += w * K.cv_s * (q.T0 - K.T_fluid);
+      if (MODE != MODE_MACROS) {
+        // momentum exchange (Eq. 28), added to the particle's integer
+        // accumulators (no reduction, no barrier; a total independent of the
+        // order): sum_i e_i f_i^eq(rho, u_s) = rho u_s, so Delta F =
+        // -f_s,p (rho u_s - j*), formed as (U_hi - j*) + (U_lo + Omega x r) + drho u_s
+        const C v0 = -w * (((q.ux - jxs) + (q.uxl + rotx)) + drho * usx);
+        const C v1 = -w * (((q.uy - jys) + (q.uyl + roty)) + drho * usy);
+        const C v2 = rx * v1 - ry * v0;
+        unsigned long long* acc = P.mes + 6 * (long long)q.id;
+        mes_add(acc, v0, B.err);
+        mes_add(acc + 2, v1, B.err);
+        mes_add(acc + 4, v2, B.err);
+      }
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = one_m * f[i] + wgt<C>(i) * (fs * drho + rho * pf[i]);
@@ -417,28 +430,6 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
   }
 
   if (MODE != MODE_MACROS) {
-    // ---- momentum-exchange sums (Eq. 28) -----------------------------------------
-    // every owned cell adds its terms to the particle's integer accumulators
-    // (no reduction, no barrier; a total independent of the order)
-#pragma unroll
-    for (int k = 0; k < MAX_OWNERS; ++k) {
-      if (k >= nown) break;
-      // sum_i e_i f_i^eq(rho, u_s) = rho u_s; Delta F = -f_s,p (rho u_s - j*),
-      // formed as (U_hi - j*) + (U_lo + Omega x r) + drho u_s (Eq. 28)
-      const PartTile<C>& q = s_p[own[k]];
-      const C rx = ((C(tx) + C(0.5)) - q.xh) - q.xl, ry = ((C(ty) + C(0.5)) - q.yh) - q.yl;
-      const C rotx = -q.om * ry, roty = q.om * rx;
-      const C usx = q.ux + (q.uxl + rotx), usy = q.uy + (q.uyl + roty);
-      const C w = ofs[k];
-      const C v0 = -w * (((q.ux - jxs) + (q.uxl + rotx)) + drho * usx);
-      const C v1 = -w * (((q.uy - jys) + (q.uyl + roty)) + drho * usy);
-      const C v2 = rx * v1 - ry * v0;
-      unsigned long long* acc = P.mes + 6 * (long long)q.id;
-      mes_add(acc, v0, B.err);
-      mes_add(acc + 2, v1, B.err);
-      mes_add(acc + 4, v2, B.err);
-    }
-
     if (!active) return np;
 
     // ---- MRT collision of f in moment space (Eqs. 3a, 4-7) ------------------
