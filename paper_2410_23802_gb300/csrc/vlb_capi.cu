@@ -442,9 +442,8 @@ static vlb_status initialize(vlb_handle* h) {
   h->K32.eps_p = h->K64.eps_p = p.contact_eps_p;
   CK(h, launch_particle_range(c, h->P, h->err_dev, h->stream));
   h->tl = 0;
-  CK(h, launch_particle_bin(c, h->P, h->TL[0], h->err_dev, h->stream));
   next_band_stamp(h);
-  CK(h, launch_particle_band(c, h->P, h->stream));
+  CK(h, launch_particle_band(c, h->P, h->TL[0], h->err_dev, h->stream));
   h->cur = 0;
   vlb_status s = launch_lattice(h, MODE_INIT, 0, 0, 0);
   if (s != VLB_OK) return s;
@@ -462,9 +461,9 @@ vlb_status vlb_step(vlb_handle* h, int32_t nsteps) {
   if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
   for (int k = 0; k < nsteps; ++k) {
     const int nl = 1 - h->tl;
-    CK(h, launch_particle_advance(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
+    CK(h, launch_particle_advance(h->PC, h->P, h->err_dev, h->stream));
     next_band_stamp(h);
-    CK(h, launch_particle_band(h->PC, h->P, h->stream));
+    CK(h, launch_particle_band(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
     const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
     if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
     if ((s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur, nl)) != VLB_OK) return s;

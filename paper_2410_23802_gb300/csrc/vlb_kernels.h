@@ -35,11 +35,10 @@ cudaError_t launch_raster_dump_f64(const LatticeConst<double>& K, const Particle
 // Particle step pieces.
 cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& P, unsigned* err,
                                   cudaStream_t st);
-cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
-                                    unsigned* err, cudaStream_t st);
-cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, cudaStream_t st);
-cudaError_t launch_particle_bin(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
-                                unsigned* err, cudaStream_t st);
+cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, unsigned* err,
+                                    cudaStream_t st);
+cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
+                                 cudaStream_t st);
 
 // FP64 audits: out[0] = sum f, out[1] = sum eps, out[2] = sum g (block partials
 // in scratch[3 * nblocks], summed in block order).

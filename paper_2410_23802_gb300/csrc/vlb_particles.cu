@@ -1,13 +1,14 @@
-// Particle kernels (Sec. 2.3), one thread per particle, FP64 throughout.
+// Particle kernels (Sec. 2.3).
 //
-//   particle_advance (one thread per particle): F_MES, T_MES of Eq. 28 from
-//     the integer accumulators the lattice kernel filled (then cleared); the
-//     inside-fluid force and torque of Eq. 29 with backward differences; the short-range contact force; Eqs. 26 and 30 by forward
-//     Euler; the tile range of the new position.
-//     The same thread then appends the particle to the tile lists of its new
-//     range (the lattice kernel sorts each list by id and finds the contact
-//     partners of the next level).
-//   particle_bin: the appending alone (initial state).
+//   particle_advance (one thread per particle, FP64): F_MES, T_MES of Eq. 28
+//     from the integer accumulators the lattice kernel filled (then cleared);
+//     the inside-fluid force and torque of Eq. 29 with backward differences;
+//     the short-range contact force; Eqs. 26 and 30 by forward Euler; the
+//     raster record and the tile range of the new position.
+//   particle_range: record and tile range of the initial state.
+//   particle_band (one warp per particle, FP32): appends the particle to the
+//     tile lists of its range (the lattice kernel sorts each list by id and
+//     finds the contact partners of the level) and fills its band table.
 #include <math.h>
 
 #include "vlb_common.cuh"
@@ -72,32 +73,9 @@ __global__ void particle_range_kernel(const ParticleConst c, const ParticleArray
   write_record(P, p, P.x[p], P.y[p], P.r[p], P.ux[p], P.uy[p], P.om[p], float(P.lam_s[p]), float(P.T0[p]));
 }
 
-// Append particle p to the lists of the tiles of range rg.  The atomics are
-// issued in batches of 8 so that their round trips overlap.
-__device__ __forceinline__ void bin_particle(const ParticleConst& c, const TileLists& TL, int p, int4 rg,
-                                             unsigned* err) {
-  const int n = rg.z * rg.w;
-  for (int t0 = 0; t0 < n; t0 += 8) {
-    int tile[8], slot[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int t = t0 + u;
-      tile[u] = t < n ? (rg.y + t / rg.z) * c.ntx + (rg.x + t % rg.z) : -1;
-      slot[u] = tile[u] >= 0 ? atomicAdd(&TL.count[tile[u]], 1) : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      if (tile[u] < 0) continue;
-      if (slot[u] < TILE_CAP) TL.ids[(long long)tile[u] * TILE_CAP + slot[u]] = p;
-      else atomicOr(err, ERR_TILE_OVERFLOW);
-    }
-  }
-}
-
 // One thread per particle: each FP64 instruction then serves 32 particles
 // (GB300's FP64 pipe is narrow, so this layout matters more than latency).
-__global__ void particle_advance_kernel(const ParticleConst c, const ParticleArrays P, const TileLists TL,
-                                        unsigned* err) {
+__global__ void particle_advance_kernel(const ParticleConst c, const ParticleArrays P, unsigned* err) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.np) return;
   const double X = P.x[p], Y = P.y[p], R = P.r[p];
@@ -194,14 +172,7 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   write_record(P, p, Xn, Yn, R, uxn, uyn, omn, lam_s, T0);
   const int4 nr = tile_range(c, Xn, Yn, R);
   P.prange[p] = nr;
-  bin_particle(c, TL, p, nr, err);
-}
-
-__global__ void particle_bin_kernel(const ParticleConst c, const ParticleArrays P, const TileLists TL,
-                                    unsigned* err) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= c.np) return;
-  bin_particle(c, TL, p, P.prange[p], err);
+  // (the band kernel that follows appends the particle to the tile lists)
 }
 
 // Exact classes and areas (Sec. 2) of the cells whose centre lies in the band
@@ -231,7 +202,8 @@ __device__ __forceinline__ void band_evaluate(const ParticleConst& c, const Part
   }
 }
 
-__global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const ParticleConst c, const ParticleArrays P) {
+__global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const ParticleConst c, const ParticleArrays P,
+                                                                        const TileLists TL, unsigned* err) {
   __shared__ int s_queue[BAND_WARPS][BAND_QUEUE];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int p = blockIdx.x * BAND_WARPS + warp;
@@ -239,6 +211,18 @@ __global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const Pa
   int* queue = s_queue[warp];
   const RasterRec rc = P.rec[p];
   const int bw = 2 * c.band_off + 1;
+  // append the particle to the lists of the tiles of its range, one lane per tile
+  {
+    const int4 rg = P.prange[p];
+    const int n = rg.z * rg.w;
+    for (int t = lane; t < n; t += 32) {
+      const int ty = t / rg.z, tx = t - ty * rg.z;
+      const int tile = (rg.y + ty) * c.ntx + (rg.x + tx);
+      const int slot = atomicAdd(&TL.count[tile], 1);
+      if (slot < TILE_CAP) TL.ids[(long long)tile * TILE_CAP + slot] = p;
+      else atomicOr(err, ERR_TILE_OVERFLOW);
+    }
+  }
   // Lane r takes row r of the box and only the cells of that row that can be
   // in the band: |x - X| between sqrt((R - 0.75)^2 - dy^2) and
   // sqrt((R + 0.75)^2 - dy^2), widened by half a cell on either side (far
@@ -313,21 +297,16 @@ cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& 
   particle_range_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, err);
   return cudaGetLastError();
 }
-cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
-                                    unsigned* err, cudaStream_t st) {
+cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, unsigned* err,
+                                    cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
-  particle_advance_kernel<<<(unsigned)((c.np + 31) / 32), 32, 0, st>>>(c, P, TL, err);
+  particle_advance_kernel<<<(unsigned)((c.np + 31) / 32), 32, 0, st>>>(c, P, err);
   return cudaGetLastError();
 }
-cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, cudaStream_t st) {
+cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
+                                 cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
-  particle_band_kernel<<<(unsigned)((c.np + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(c, P);
-  return cudaGetLastError();
-}
-cudaError_t launch_particle_bin(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
-                                unsigned* err, cudaStream_t st) {
-  if (c.np == 0) return cudaSuccess;
-  particle_bin_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, TL, err);
+  particle_band_kernel<<<(unsigned)((c.np + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(c, P, TL, err);
   return cudaGetLastError();
 }
 }  // namespace vlb
