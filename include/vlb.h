@@ -126,6 +126,16 @@ vlb_status vlb_params_default(vlb_params* p);
  * sizes, unknown precision), VLB_ENOMEM, VLB_ECUDA. */
 vlb_status vlb_create(const vlb_params* p, vlb_handle** out);
 
+/* Hold particles [first, first + n) at their temperature T0 (held[k] != 0)
+ * or let them conduct (held[k] == 0, the default): the paper's first
+ * sedimentation case of Sec. 3.4 keeps the particle "at T_c".  Reading: in
+ * the part of a cell such a particle covers, the thermal populations are
+ * replaced by the equilibrium at T0 in the volumetric form of Eq. 8,
+ * g = (1 - f_fix) g + sum_p f_s,p g^eq(c_vs T0_p, T0_p).  Only before the
+ * first vlb_step (VLB_ESTATE afterwards); VLB_EINVAL for a range outside the
+ * particles added so far. */
+vlb_status vlb_set_fixed_temperature(vlb_handle* h, int32_t first, int32_t n, const int32_t* held);
+
 /* Queue all further work of h on cuda_stream (a cudaStream_t; NULL selects
  * the legacy default stream).  Pending work on the previous stream is
  * synchronised first. */

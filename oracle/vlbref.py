@@ -436,6 +436,31 @@ def geq(eps, T, cref):
     return from_moments(thermal_eq_moments(eps, T, cref))
 
 
+def fixed_temperature_correction(g, ras, T_p, fixed, cv_s, cref):
+    """Particles held at their own temperature (Sec. 3.4, first case: "the
+    temperatures of the solid particle ... are kept at T_c"; reading R11): in
+    the part of a cell that such a particle covers, the thermal populations
+    are replaced by the equilibrium at the particle's temperature, in the
+    volumetric form of Eq. 8:
+        g = (1 - f_fix) g + sum_{p fixed} f_s,p g^eq(c_vs T_p, T_p),
+    f_fix = sum_{p fixed} f_s,p.  Particles not held (fixed[p] False) keep
+    the conjugate treatment."""
+    ffix = np.zeros(g.shape[1:])
+    acc = np.zeros_like(g)
+    for k in range(MAX_OWNERS):
+        sel = ras.count > k
+        if not sel.any():
+            continue
+        own = np.where(sel, ras.owner[:, :, k], 0)
+        w = np.where(sel & fixed[own], ras.fsp[:, :, k], 0.0)
+        if not w.any():
+            continue
+        Tp = T_p[own]
+        ffix = ffix + w
+        acc = acc + w * geq(cv_s * Tp, Tp, cref)
+    return (1.0 - ffix) * g + acc
+
+
 def tau_g_of(lam, cref, rho_f=1.0):
     """tau_g from Eq. 22: lambda / rho_f = (4 + alpha1)/6 c_ref (tau_g - 1/2)."""
     return 0.5 + 6.0 * lam / ((4.0 + ALPHA1) * rho_f * cref)
@@ -627,10 +652,13 @@ class Simulation:
     with its owners; [df_s/dt]^n; per particle X, theta, U, Omega, the
     previous U, Omega and the hydrodynamic force and torque of level n."""
 
-    def __init__(self, prm: Params, x, y, radius, T0, k_ratio=None, ux=None, uy=None, omega=None):
+    def __init__(self, prm: Params, x, y, radius, T0, k_ratio=None, ux=None, uy=None, omega=None,
+                 fixed_T=None):
         self.prm = prm
         n = len(x)
         z = np.zeros(n)
+        # particles held at their initial temperature T0 (reading R11)
+        self.fixed_T = np.array(fixed_T if fixed_T is not None else np.zeros(n), dtype=bool)
         self.part = {
             "x": np.array(x, dtype=float), "y": np.array(y, dtype=float),
             "r": np.array(radius, dtype=float), "T0": np.array(T0, dtype=float),
@@ -750,6 +778,8 @@ class Simulation:
         self.ras = self._raster()
         # (4) volumetric correction and momentum exchange (Eqs. 8, 28)
         self.f, self.F_mes, self.T_mes = correct_and_exchange(fstar, self.ras, self.part)
+        if self.fixed_T.any():
+            g = fixed_temperature_correction(g, self.ras, self.part["T0"], self.fixed_T, p.cv_s, p.cref)
         # (5) thermal macroscopics at n+1 (Eqs. 11, 21-25) jointly with rho, u (Eq. 9)
         self.dfs = dfs_dt_update(self.ras.fs, fs_old, self.dfs)
         self.cv, lam = self._properties(self.ras)

@@ -46,6 +46,7 @@ struct vlb_handle {
   // particles
   int np = 0, cap = 0;
   std::vector<double> hx, hy, hr, hT0, hk, hux, huy, hom;
+  std::vector<int> hfix;  // particles held at their temperature
   ParticleArrays P{};
   TileLists TL[2] = {};
   int tl = 0;  // list buffer of the current level
@@ -255,14 +256,14 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     if ((e = cudaMalloc(&h->TL[b].ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
     cudaMemsetAsync(h->TL[b].count, 0, ntiles * sizeof(int), h->stream);
   }
-  // particle arrays: 15 doubles, one int4, NBR_CAP + 1 ints, 2 NBR_CAP + 8
-  // doubles and one raster record per particle; every sub-array starts on a
+  // particle arrays: 15 doubles, one int4, NBR_CAP + 2 ints, 8 doubles and
+  // one raster record per particle; every sub-array starts on a
   // 256-byte boundary (int4 and record loads need 16-byte alignment)
   const size_t capn = (size_t)std::max(h->cap, 1);
   auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t pbytes = 15 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) +
                         a256(capn * sizeof(int)) + a256(capn * NBR_CAP * sizeof(int)) +
-                        a256(capn * NBR_CAP * 2 * sizeof(double)) + a256(capn * 8 * sizeof(double)) +
+                        a256(capn * sizeof(int)) + a256(capn * 8 * sizeof(double)) +
                         a256(capn * sizeof(RasterRec));
   if ((e = cudaMalloc(&h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
   h->pbytes = pbytes;
@@ -275,7 +276,7 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     h->P.prange = reinterpret_cast<int4*>(b); b += a256(capn * sizeof(int4));
     h->P.nbr_count = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.nbr = reinterpret_cast<int*>(b); b += a256(capn * NBR_CAP * sizeof(int));
-    h->P.nbr_f = reinterpret_cast<double*>(b); b += a256(capn * NBR_CAP * 2 * sizeof(double));
+    h->P.fixed_T = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.pk = reinterpret_cast<double*>(b); b += a256(capn * 8 * sizeof(double));
     h->P.rec = reinterpret_cast<RasterRec*>(b);
   }
@@ -291,6 +292,15 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   cudaMemsetAsync(h->err_dev, 0, sizeof(unsigned), h->stream);
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(e, "create sync");
   *out = h;
+  return VLB_OK;
+}
+
+vlb_status vlb_set_fixed_temperature(vlb_handle* h, int32_t first, int32_t n, const int32_t* held) {
+  if (!h) return VLB_EINVAL;
+  if (h->initialized) return fail(h, VLB_ESTATE, "fixed temperatures must be set before the first step");
+  if (first < 0 || n < 0 || first + n > h->np || (n > 0 && !held))
+    return fail(h, VLB_EINVAL, "vlb_set_fixed_temperature: particle range outside the added particles");
+  for (int k = 0; k < n; ++k) h->hfix[first + k] = held[k] != 0;
   return VLB_OK;
 }
 
@@ -340,6 +350,7 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
     h->hr.push_back(radius[k]);
     h->hT0.push_back(T0[k]);
     h->hk.push_back(k_ratio ? k_ratio[k] : p.k_ratio_default);
+    h->hfix.push_back(0);
     h->hux.push_back(uv ? uv[2 * k] : 0.0);
     h->huy.push_back(uv ? uv[2 * k + 1] : 0.0);
     h->hom.push_back(omega ? omega[k] : 0.0);
@@ -401,6 +412,7 @@ static vlb_status initialize(vlb_handle* h) {
     CK(h, cudaMemcpyAsync(h->P.r, h->hr.data(), b, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->P.T0, h->hT0.data(), b, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->P.lam_s, lam.data(), b, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->P.fixed_T, h->hfix.data(), n * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->P.ux, h->hux.data(), b, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->P.uy, h->huy.data(), b, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->P.om, h->hom.data(), b, cudaMemcpyHostToDevice, h->stream));

@@ -79,10 +79,10 @@ struct ParticleArrays {
   double *fcx, *fcy, *tc;  // F_c, T_c of the last update
   double *r, *lam_s, *T0;  // radius, lambda_s, initial temperature
   int4* prange;            // tile range (tx0, ty0, ntx, nty) at the current level
-  unsigned long long* mes; // [n][3][2] F_MES,x, F_MES,y, T_MES as fixed point (see mes_add)
+  unsigned long long* mes; // [n][3][2] F_MES,x + contact x, F_MES,y + contact y, T_MES as fixed point (mes_add)
   int* nbr_count;          // contact partners per particle
   int* nbr;                // [n][NBR_CAP], unordered (sorted where used)
-  double* nbr_f;           // [n][NBR_CAP][2] contact force on the particle from that partner
+  int* fixed_T;            // [n] 1: the particle is held at its temperature T0 (reading R11)
   double* pk;              // [n][8] constants: 1/M, 1/I, M_in, I_in, body force factor, wall factor
   RasterRec* rec;          // [n] raster records of the current level
   int2* band;              // [n][bw][bw] band tables: (class | stamp << 2, area bits) of the cells of

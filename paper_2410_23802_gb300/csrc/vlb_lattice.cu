@@ -85,6 +85,7 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
       tile_geometry(rc, x0, y0, q);
       q.ux = rc.ux; q.uxl = rc.uxl; q.uy = rc.uy; q.uyl = rc.uyl; q.om = rc.om;
       q.lam_s = rc.lam_s; q.T0 = rc.T0;
+      q.fixed = P.fixed_T[id];
     } else {
       const double X = P.x[id] - double(x0), Y = P.y[id] - double(y0), R = P.r[id];
       const long long Q = 1ll << QBITS;
@@ -101,6 +102,7 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
       q.uxl = C(P.ux[id] - double(q.ux)); q.uyl = C(P.uy[id] - double(q.uy));
       q.lam_s = C(P.lam_s[id]); q.T0 = C(P.T0[id]);
       q.ci = 0; q.cj = 0;
+      q.fixed = P.fixed_T[id];
     }
     q.id = id;
     const int4 rg = P.prange[id];
@@ -274,18 +276,20 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
         fx = mag * dx;
         fy = mag * dy;
       }
+      // the force goes into both particles' integer force accumulators (+F on
+      // i, -F on j: exact negation, so F_ji = -F_ij and the sum over all
+      // pairs does not depend on the order); the partner lists are kept for
+      // inspection
+      if (fx != 0.0 || fy != 0.0) {
+        mes_add(P.mes + 6 * (long long)i, fx, B.err);
+        mes_add(P.mes + 6 * (long long)i + 2, fy, B.err);
+        mes_add(P.mes + 6 * (long long)j, -fx, B.err);
+        mes_add(P.mes + 6 * (long long)j + 2, -fy, B.err);
+      }
       const int si = atomicAdd(&P.nbr_count[i], 1);
       const int sj = atomicAdd(&P.nbr_count[j], 1);
-      if (si < NBR_CAP) {
-        P.nbr[i * NBR_CAP + si] = j;
-        P.nbr_f[2 * (i * NBR_CAP + si)] = fx;
-        P.nbr_f[2 * (i * NBR_CAP + si) + 1] = fy;
-      }
-      if (sj < NBR_CAP) {
-        P.nbr[j * NBR_CAP + sj] = i;
-        P.nbr_f[2 * (j * NBR_CAP + sj)] = -fx;
-        P.nbr_f[2 * (j * NBR_CAP + sj) + 1] = -fy;
-      }
+      if (si < NBR_CAP) P.nbr[i * NBR_CAP + si] = j;
+      if (sj < NBR_CAP) P.nbr[j * NBR_CAP + sj] = i;
       if (si >= NBR_CAP || sj >= NBR_CAP) atomicOr(B.err, ERR_NBR_OVERFLOW);
     }
 
@@ -323,6 +327,7 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
 #pragma unroll
     for (int i = 0; i < 9; ++i) pf[i] = C(0);
     C cjx = one_m * jx, cjy = one_m * jy;
+    C hfix = C(0), h0 = C(0), hr = C(0);  // held owners: covered fraction, g^eq deviations
     const C xc = C(tx) + C(0.5), yc = C(ty) + C(0.5);
 #pragma unroll
     for (int k = 0; k < MAX_OWNERS; ++k) {
@@ -341,6 +346,14 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
       cjx += w * rho * usx;
       cjy += w * rho * usy;
       lam += w * q.lam_s;
+      if (q.fixed) {
+        // held at T_p = T0 (reading R11): its part of the cell takes
+        // g^eq(c_vs T_p, T_p), here as the deviation from g^eq(eps_f, T_f)
+        const C dTp = q.T0 - K.T_fluid;
+        hfix += w;
+        h0 += w * ((K.cv_s * q.T0 - K.cv_f * K.T_fluid) - C(5.0 / 9.0) * K.cref * dTp);
+        hr += w * K.cref * dTp;
+      }
       dT_init += w * K.cv_s * (q.T0 - K.T_fluid);
       if (MODE != MODE_MACROS) {
         // momentum exchange (Eq. 28), added to the particle's integer
@@ -360,6 +373,12 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
     for (int i = 0; i < 9; ++i) f[i] = one_m * f[i] + wgt<C>(i) * (fs * drho + rho * pf[i]);
     jx = cjx;
     jy = cjy;
+    if (hfix > C(0)) {  // g = (1 - f_fix) g + sum over held owners of f_s,p g^eq(c_vs T_p, T_p)
+      const C keep = C(1) - hfix;
+      g[0] = keep * g[0] + h0;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) g[i] = keep * g[i] + wgt<C>(i) * hr;
+    }
   }
 
   // ---- thermal macroscopics at n+1 (Eqs. 11, 16, 21-25) ----------------------

@@ -87,9 +87,9 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   const double ux_prev = P.ux_prev[p], uy_prev = P.uy_prev[p], om_prev = P.om_prev[p];
   const double theta = P.theta[p];
   const float lam_s = float(P.lam_s[p]), T0 = float(P.T0[p]);
-  // momentum-exchange force and torque of the current level (Eq. 28): the
-  // lattice kernel's integer accumulators, read and cleared for the next level
-  const int ncount = P.nbr_count[p];
+  // momentum-exchange force and torque of the current level (Eq. 28) plus the
+  // particle-particle contact forces of that level: the lattice kernel's
+  // integer accumulators, read and cleared for the next level
   unsigned long long* acc = P.mes + 6 * (long long)p;
   const ulonglong2 a0 = reinterpret_cast<const ulonglong2*>(acc)[0];
   const ulonglong2 a1 = reinterpret_cast<const ulonglong2*>(acc)[1];
@@ -98,40 +98,9 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   reinterpret_cast<ulonglong2*>(acc)[0] = make_ulonglong2(0ull, 0ull);
   reinterpret_cast<ulonglong2*>(acc)[1] = make_ulonglong2(0ull, 0ull);
   reinterpret_cast<ulonglong2*>(acc)[2] = make_ulonglong2(0ull, 0ull);
-  // contact force: partner forces (computed at this level by the lattice
-  // kernel) summed in ascending partner id, then walls x-, x+, y-, y+
+  P.nbr_count[p] = 0;  // the lattice kernel of this step lists the next partners
+  // wall contact forces: walls x-, x+, y-, y+
   double Fc_x = 0.0, Fc_y = 0.0;
-  {
-    int nb[NBR_CAP];
-    double nfx[NBR_CAP], nfy[NBR_CAP];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      nb[a] = P.nbr[p * NBR_CAP + a];
-      nfx[a] = P.nbr_f[2 * (p * NBR_CAP + a)];
-      nfy[a] = P.nbr_f[2 * (p * NBR_CAP + a) + 1];
-    }
-    const int nn = min(ncount, NBR_CAP);
-    for (int a = 4; a < nn; ++a) {
-      nb[a] = P.nbr[p * NBR_CAP + a];
-      nfx[a] = P.nbr_f[2 * (p * NBR_CAP + a)];
-      nfy[a] = P.nbr_f[2 * (p * NBR_CAP + a) + 1];
-    }
-    if (nn > 0) {
-      // insertion sort by partner id
-      for (int a = 1; a < nn; ++a) {
-        const int j = nb[a];
-        const double fx = nfx[a], fy = nfy[a];
-        int q = a;
-        while (q > 0 && nb[q - 1] > j) { nb[q] = nb[q - 1]; nfx[q] = nfx[q - 1]; nfy[q] = nfy[q - 1]; --q; }
-        nb[q] = j; nfx[q] = fx; nfy[q] = fy;
-      }
-      P.nbr_count[p] = 0;  // the lattice kernel of this step lists the next partners
-      for (int a = 0; a < nn; ++a) {
-        Fc_x += nfx[a];
-        Fc_y += nfy[a];
-      }
-    }
-  }
   {
     const double dist[4] = {X, double(c.nx) - X, Y, double(c.ny) - Y};
     const double nxw[4] = {1.0, -1.0, 0.0, 0.0}, nyw[4] = {0.0, 0.0, 1.0, -1.0};
@@ -146,6 +115,7 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
     }
   }
   // Eqs. 26, 29, 30: F_c = F_MES - F_in + (rho_s - rho_f) V g + F_contact
+  // (Fm_x, Fm_y carry the particle-particle part of F_contact)
   const double Fin_x = -k[2] * (ux - ux_prev);
   const double Fin_y = -k[2] * (uy - uy_prev);
   const double Tin = -k[3] * (om - om_prev);

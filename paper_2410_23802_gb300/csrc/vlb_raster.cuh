@@ -64,6 +64,7 @@ struct PartTile {
   C lam_s, T0;
   int id;                 // particle id
   int ci, cj;             // cell of the centre (band table origin)
+  int fixed;              // held at its temperature T0 (reading R11)
   int rx, ry;             // first tile of the particle's range
 };
 

@@ -74,6 +74,7 @@ def _load():
         "vlb_params_default": (ctypes.c_int, [P(vlb_params)]),
         "vlb_create": (ctypes.c_int, [P(vlb_params), P(ctypes.c_void_p)]),
         "vlb_set_stream": (ctypes.c_int, [h, ctypes.c_void_p]),
+        "vlb_set_fixed_temperature": (ctypes.c_int, [h, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
         "vlb_add_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
         "vlb_step": (ctypes.c_int, [h, ctypes.c_int32]),
         "vlb_synchronize": (ctypes.c_int, [h]),
@@ -237,6 +238,12 @@ def vlb_get_contact_pairs(h) -> np.ndarray:
     buf = np.empty(2 * max(n.value, 1), dtype=np.int32)
     _check(_lib.vlb_get_contact_pairs(h, n.value, _ptr(buf, ctypes.c_int32), ctypes.byref(n)), h)
     return buf[: 2 * n.value].reshape(-1, 2)
+
+
+def vlb_set_fixed_temperature(h, held, first: int = 0) -> None:
+    """Hold particles first .. first + len(held) - 1 at their temperature T0 where held is true."""
+    a = np.ascontiguousarray(np.asarray(held, dtype=np.int32))
+    _check(_lib.vlb_set_fixed_temperature(h, int(first), int(a.size), _ptr(a, ctypes.c_int32)), h)
 
 
 def vlb_state_size(h) -> int:

@@ -54,6 +54,7 @@ class Case:
     radius: list
     T0: list
     k_ratio: list | None = None
+    fixed_T: list | None = None   # particles held at their temperature T0
 
     @property
     def cells(self) -> int:
@@ -110,6 +111,26 @@ def channel(precision: str = "fp64") -> Case:
                   thermal_wall=(0, 0, 0, 0), wall_T=(0.0, 0.0, 0.0, 0.0), thermal_rates_mode=0,
                   precision=precision)
     return Case("channel 100x400, 1 disk D=20", params, [50.0], [300.0], [10.0], [0.0])
+
+
+def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision: str = "fp32") -> Case:
+    """Sedimentation of a disk held at T_c = 0 in a long channel (the paper's
+    first Sec. 3.4 case, Table 4): D = 20 lu, width 4D, the disk starting D/2
+    left of the centreline (x = 1.5 D), rho_r = 1.00232, Re = 40.5, Pr = 0.7,
+    Grashof number gr, tau_f = 0.53, R_lambda = R_cv = 1; fluid and walls at
+    T_h = 1 (T_ref = T_h).  The channel length is not given (length_d
+    diameters; the disk starts 10 D below the top)."""
+    D = 20.0
+    nu = (0.53 - 0.5) / 3.0
+    u_ref = 40.5 * nu / D
+    g = u_ref ** 2 / ((1.00232 - 1.0) * math.pi * D / 2.0)
+    nx, ny = int(4 * D), int(length_d * D)
+    params = dict(nx=nx, ny=ny, tau_f=0.53, prandtl=0.7, rho_ratio=1.00232, cv_ratio=1.0,
+                  k_ratio_default=1.0, gravity=(0.0, -g), beta=gr_beta(gr, nu, g, 1.0, D), T_ref=1.0,
+                  T_fluid_init=1.0, thermal_wall=(1, 1, 1, 1), wall_T=(1.0, 1.0, 1.0, 1.0),
+                  thermal_rates_mode=0, precision=precision)
+    return Case(f"fixed-temperature sedimentation {nx}x{ny}, Gr={gr:g}", params, [1.5 * D], [ny - 10.0 * D],
+                [D / 2.0], [0.0], None, [1])
 
 
 def conjugate_sedimentation(r_cv: float, length_d: float = 40.0, precision: str = "fp32") -> Case:

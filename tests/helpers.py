@@ -16,6 +16,8 @@ def gpu_lattice(case, precision=None, max_particles=None, **over):
     if n:
         xy = np.column_stack([case.x, case.y])
         lat.add_particles(xy, case.radius, case.T0, k_ratio=case.k_ratio)
+        if getattr(case, "fixed_T", None) is not None:
+            V.vlb_set_fixed_temperature(lat.h, case.fixed_T)
     return lat
 
 
@@ -25,7 +27,8 @@ def oracle_sim(case, **over):
     prm.update(over)
     if "periodic" in prm:
         prm["periodic"] = tuple(bool(v) for v in prm["periodic"])
-    return O.Simulation(O.Params(**prm), case.x, case.y, case.radius, case.T0, k_ratio=case.k_ratio)
+    return O.Simulation(O.Params(**prm), case.x, case.y, case.radius, case.T0, k_ratio=case.k_ratio,
+                        fixed_T=getattr(case, "fixed_T", None))
 
 
 def rel_l2(a, b):

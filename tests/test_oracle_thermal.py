@@ -137,3 +137,33 @@ def test_paper_cavity_balance_temperature():
     cvs = gold["R_cv"]
     teq = ((1 - phi) * 1.0 * gold["T_h"] + phi * cvs * gold["T_c"]) / ((1 - phi) + phi * cvs)
     assert abs(teq - gold["T_eq"]) < 5e-5
+
+
+def _fixed_T_sim(ux=0.0, T_p=0.0, beta=0.0, walls=(1, 1, 1, 1), wall_T=1.0):
+    p = V.Params(nx=48, ny=48, tau_f=0.8, prandtl=0.7, rho_ratio=1.0, cv_ratio=1.0, k_ratio_default=1.0,
+                 gravity=(0.0, -1e-5), beta=beta, T_ref=1.0, T_fluid_init=1.0, thermal_wall=walls,
+                 wall_T=(wall_T,) * 4)
+    return V.Simulation(p, [20.3], [24.6], [7.0], [T_p], ux=[ux], fixed_T=[True])
+
+
+def test_fixed_temperature_particle_interior_stays_at_its_temperature():
+    """Reading R11: cells a held particle covers completely carry the
+    equilibrium at its temperature, so their T is exactly T_p (the gradient
+    of an equilibrium vanishes and c_vs = c_vf leaves no source term)."""
+    sim = _fixed_T_sim(T_p=0.25)
+    sim.step(40)
+    inside = sim.ras.fs == 1.0
+    assert inside.sum() > 100
+    assert np.abs(sim.T[inside] - 0.25).max() < 1e-13
+    # the fluid around it cools towards it, between T_p and the walls
+    assert sim.T.min() >= 0.25 - 1e-12 and sim.T.max() <= 1.0 + 1e-12
+    assert (sim.T[~inside] < 1.0 - 1e-6).any()
+
+
+def test_fixed_temperature_particle_at_fluid_temperature_changes_nothing():
+    """A held particle at the fluid and wall temperature, moving through the
+    fluid, leaves T uniform to rounding (nothing in the correction acts on
+    a uniform temperature field)."""
+    sim = _fixed_T_sim(ux=0.02, T_p=1.0)
+    sim.step(60)
+    assert np.abs(sim.T - 1.0).max() < 1e-12
