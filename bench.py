@@ -38,6 +38,25 @@ def _dist():
     return rank, world, local
 
 
+def _max_over_ranks(x: float) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    rank's); x itself without a process group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_mlups(world: int, cells: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank advances its own replica of `cells`
+    by `steps` steps (weak scaling); the job takes the slowest rank's time."""
+    return world * cells * steps / seconds / 1e6
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -169,10 +188,8 @@ def run_ours(args):
         clocks = sampler.stop()
     elapsed_ms = t0.elapsed_time(t1)
     lattice_ms, lattice_launches, launches_per_step = V.vlb_profile_end(lat.h)
+    elapsed_ms = _max_over_ranks(elapsed_ms)
     if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         torch.distributed.barrier()
     lat.close()
 
@@ -191,16 +208,13 @@ def run_ours(args):
     e2e_s = time.perf_counter() - w0
     lat2.close()
     assert np.isfinite(fields["T"]).all() and np.isfinite(parts["y"]).all()
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = _max_over_ranks(e2e_s)
     h2d = len(case.x) * (2 * 8 + 3 * 8)          # centres, radius, T0, k_ratio
     d2h = cells * 5 * 8 + len(case.x) * 9 * 8   # five fields and the particle state, FP64
 
     if rank != 0:
         return
-    value = world * cells * args.steps / (elapsed_ms * 1e-3) / 1e6
+    value = _job_mlups(world, cells, args.steps, elapsed_ms * 1e-3)
     peak, peak_kind = _peaks()
     lattice_avg_s = lattice_ms * 1e-3 / max(lattice_launches, 1)
     bpc = BYTES_PER_CELL[args.precision]
@@ -227,7 +241,7 @@ def run_ours(args):
                      "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(key),
                      "kernel": "lattice_kernel<STEP>", "bytes_per_cell": bpc, "peak_kind": peak_kind,
                      "avg_launch_us": round(lattice_avg_s * 1e6, 2)},
-        "e2e": {"value": round(world * cells * e2e_steps / e2e_s / 1e6, 1), "unit": UNIT,
+        "e2e": {"value": round(_job_mlups(world, cells, e2e_steps, e2e_s), 1), "unit": UNIT,
                 "h2d_bytes_per_step": round(h2d / e2e_steps, 1), "d2h_bytes_per_step": round(d2h / e2e_steps, 1),
                 "note": "create + host particle upload + steps + fields and particle state to host, wall clock"},
         "gpu_launches": launches_per_step * args.steps,
