@@ -444,6 +444,9 @@ static vlb_status initialize(vlb_handle* h) {
   c.ntx = h->ntx; c.nty = h->nty;
   c.band_off = band_off;
   h->K32.band_off = h->K64.band_off = band_off;
+  int any_held = 0;
+  for (int v : h->hfix) any_held |= v;
+  h->K32.any_held = h->K64.any_held = any_held;
   c.rho_ratio = p.rho_ratio; c.gx = p.gravity[0]; c.gy = p.gravity[1];
   c.zeta = p.contact_range; c.eps_p = p.contact_eps_p; c.eps_w = p.contact_eps_w;
   c.contact_scale = std::fabs(p.rho_ratio - 1.0) * std::hypot(p.gravity[0], p.gravity[1]) * M_PI;
@@ -783,6 +786,11 @@ vlb_status vlb_load_state(vlb_handle* h, const void* buf, uint64_t bytes) {
     CK(h, put(h->TL[b].count, I.tl_count_bytes));
     CK(h, put(h->TL[b].ids, I.tl_ids_bytes));
   }
+  // the held-temperature flags came with the particle block
+  if (h->np > 0) CK(h, cudaMemcpy(h->hfix.data(), h->P.fixed_T, h->np * sizeof(int), cudaMemcpyDeviceToHost));
+  int any_held = 0;
+  for (int v : h->hfix) any_held |= v;
+  h->K32.any_held = h->K64.any_held = any_held;
   h->cur = I.cur;
   h->tl = I.tl;
   h->step = I.step;

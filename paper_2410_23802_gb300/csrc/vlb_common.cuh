@@ -147,6 +147,7 @@ struct LatticeConst {
   int per_x, per_y;        // periodic axes
   int band_off;            // half-width of the band tables (cells)
   int band_stamp;          // level stamp the band tables must carry
+  int any_held;            // some particle is held at its temperature (reading R11)
   int wall_dirichlet[4];   // x-, x+, y-, y+
   int np;
   double zeta;             // contact range

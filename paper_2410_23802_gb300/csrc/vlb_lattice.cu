@@ -238,7 +238,7 @@ __device__ __forceinline__ void pull_direct(const LatticeConst<C>& K, const Step
 // list, f_s and owners, correction, thermal macroscopics, exchange sums,
 // both collisions and the stores.  Called by every thread of the CTA (it has
 // barriers); returns the tile's particle count.
-template <class S, class C, int MODE>
+template <class S, class C, int MODE, bool HOLD>
 __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuffers& B, const ParticleArrays& P,
                                          const TileLists& TL, int tile_x, int tile_y, C (&f)[9], C (&g)[9],
                                          const C s_old, TileShared<C>& sh) {
@@ -346,7 +346,7 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
       cjx += w * rho * usx;
       cjy += w * rho * usy;
       lam += w * q.lam_s;
-      if (q.fixed) {
+      if (HOLD && q.fixed) {
         // held at T_p = T0 (reading R11): its part of the cell takes
         // g^eq(c_vs T_p, T_p), here as the deviation from g^eq(eps_f, T_f)
         const C dTp = q.T0 - K.T_fluid;
@@ -373,7 +373,7 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
     for (int i = 0; i < 9; ++i) f[i] = one_m * f[i] + wgt<C>(i) * (fs * drho + rho * pf[i]);
     jx = cjx;
     jy = cjy;
-    if (hfix > C(0)) {  // g = (1 - f_fix) g + sum over held owners of f_s,p g^eq(c_vs T_p, T_p)
+    if (HOLD && hfix > C(0)) {  // g = (1 - f_fix) g + sum over held owners of f_s,p g^eq(c_vs T_p, T_p)
       const C keep = C(1) - hfix;
       g[0] = keep * g[0] + h0;
 #pragma unroll
@@ -546,13 +546,13 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
   return np;
 }
 
-template <class S, class C, int MODE>
+template <class S, class C, int MODE, bool HOLD>
 __global__ void __launch_bounds__(TILE_X * TILE_Y, sizeof(C) == 4 ? VLB_LATTICE_MIN_BLOCKS : 1)
 lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArrays P, const TileLists TL) {
   __shared__ TileShared<C> sh;
   C f[9], g[9], s_old;
   pull_direct<S, C, MODE>(K, B, blockIdx.x, blockIdx.y, f, g, s_old);
-  cell_body<S, C, MODE>(K, B, P, TL, blockIdx.x, blockIdx.y, f, g, s_old, sh);
+  cell_body<S, C, MODE, HOLD>(K, B, P, TL, blockIdx.x, blockIdx.y, f, g, s_old, sh);
 }
 
 // Ownership of every cell at the current level, from the same raster code as
@@ -629,9 +629,12 @@ template <class S, class C>
 static cudaError_t launch_mode(int mode, const LatticeConst<C>& K, const StepBuffers& B,
                                const ParticleArrays& P, const TileLists& TL, cudaStream_t st) {
   dim3 grid(K.ntx, K.nty), block(TILE_X, TILE_Y);
-  if (mode == MODE_INIT) lattice_kernel<S, C, MODE_INIT><<<grid, block, 0, st>>>(K, B, P, TL);
-  else if (mode == MODE_STEP) lattice_kernel<S, C, MODE_STEP><<<grid, block, 0, st>>>(K, B, P, TL);
-  else lattice_kernel<S, C, MODE_MACROS><<<grid, block, 0, st>>>(K, B, P, TL);
+  // kernels with the held-temperature path only where some particle is held
+  if (mode == MODE_INIT) lattice_kernel<S, C, MODE_INIT, false><<<grid, block, 0, st>>>(K, B, P, TL);
+  else if (mode == MODE_STEP && K.any_held) lattice_kernel<S, C, MODE_STEP, true><<<grid, block, 0, st>>>(K, B, P, TL);
+  else if (mode == MODE_STEP) lattice_kernel<S, C, MODE_STEP, false><<<grid, block, 0, st>>>(K, B, P, TL);
+  else if (K.any_held) lattice_kernel<S, C, MODE_MACROS, true><<<grid, block, 0, st>>>(K, B, P, TL);
+  else lattice_kernel<S, C, MODE_MACROS, false><<<grid, block, 0, st>>>(K, B, P, TL);
   return cudaGetLastError();
 }
 
