@@ -30,9 +30,12 @@ def _assert_same(a, b):
         assert np.array_equal(pa[k], pb[k]), k
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_resume_continues_bit_for_bit(tmp_path, precision):
+@pytest.mark.parametrize("precision,held", [("fp32", False), ("fp64", False), ("fp32", True)])
+def test_resume_continues_bit_for_bit(tmp_path, precision, held):
+    import dataclasses
     case = W.cavity(side=128, n=16, seed=11, k_log_uniform=True)
+    if held:  # the held flags travel with the image (the fresh handle does not set them)
+        case = dataclasses.replace(case, fixed_T=[k % 3 == 0 for k in range(16)])
     with gpu_lattice(case, precision=precision) as a:
         a.step(N_BEFORE)
         path = tmp_path / "state.bin"
@@ -40,8 +43,9 @@ def test_resume_continues_bit_for_bit(tmp_path, precision):
         a.step(N_AFTER)
         ref = _snapshot(a)
     # from the in-memory image and from the file, each into a fresh handle
+    fresh = dataclasses.replace(case, fixed_T=None)
     for source in (img, str(path)):
-        with gpu_lattice(case, precision=precision) as b:
+        with gpu_lattice(fresh, precision=precision) as b:
             b.load_state(source)
             b.step(N_AFTER)
             _assert_same(_snapshot(b), ref)
