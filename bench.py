@@ -1,6 +1,7 @@
 """Throughput of the coupled flow + thermal + particle step on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload cavity|channels]
 
 Workload (default): 2048 cold disks (D = 16 lu) in a 2048 x 2048 cavity, FP32
 (the seeded synthetic case of paper_2410_23802_gb300.workloads.cavity).  One
@@ -9,6 +10,12 @@ fraction, f and g collide/stream with the volumetric correction, MES partial
 sums.  Metric: coupled MLUPS (one lattice update = f and g at one cell).
 Under torchrun each rank runs its own replica of the case on its GPU (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
+
+--workload channels: 256 independent single-disk channels (widths 64..256,
+4 widths long; workloads.channels), all resident, stepped together with
+vlb_step_batch (one launch of each kernel per step for all cases), against
+the same cases on their own streams and one after the other with vlb_step.
+One JSON line, 1 GPU.
 """
 from __future__ import annotations
 
@@ -252,6 +259,100 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_channels(args):
+    """Many small cases at once: one launch of each kernel per step for all
+    cases (vlb_step_batch), against the same cases on their own streams with
+    vlb_step, and one after the other on one stream (the plain path)."""
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")  # hardware queues for the streams leg
+    import torch
+    from paper_2410_23802_gb300 import vlb as V
+    from paper_2410_23802_gb300 import workloads as W
+
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    cases = W.channels(n=args.cases, precision=args.precision)
+    cells = sum(c.cells for c in cases)
+    main_stream = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in cases]
+    lats = []
+    for c, st in zip(cases, streams):
+        lat = V.Lattice(_params(c, V))
+        V.vlb_set_stream(lat.h, st.cuda_stream)
+        lat.add_particles(list(zip(c.x, c.y)), c.radius, c.T0, k_ratio=c.k_ratio)
+        lats.append(lat)
+    hs = [l.h for l in lats]
+
+    def timed(run):
+        """Device time from an event on main_stream that every case stream
+        waits for to one main_stream records after waiting for all of them."""
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(main_stream)
+        for st in streams:
+            st.wait_event(t0)
+        run()
+        for st in streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            main_stream.wait_event(ev)
+        t1.record(main_stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
+
+    mlups = lambda ms: cells * args.steps / (ms * 1e-3) / 1e6  # noqa: E731
+    V.vlb_step_batch(hs, args.warmup)
+    for l in lats:
+        V.vlb_synchronize(l.h)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    batched_ms = timed(lambda: V.vlb_step_batch(hs, args.steps))
+    clocks = sampler.stop()
+    wall0 = time.perf_counter()
+    V.vlb_step_batch(hs, args.steps)
+    for l in lats:
+        V.vlb_synchronize(l.h)
+    host_s = time.perf_counter() - wall0
+    streams_ms = timed(lambda: [l.step(args.steps) for l in lats])
+    for l in lats:  # the plain path: one stream, one case after the other
+        V.vlb_set_stream(l.h, streams[0].cuda_stream)
+    plain_ms = timed(lambda: [l.step(args.steps) for l in lats])
+    for l in lats:
+        l.close()
+    value = mlups(batched_ms)
+    line = {
+        "metric": METRIC + " (batched independent cases)",
+        "value": round(value, 1),
+        "unit": UNIT,
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(batched_ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f16 storage / f32", "bf16": "bf16 storage / f32"}[
+            args.precision],
+        "data": "synthetic (seeded SplitMix64 widths and parameters)",
+        "config": {"workload": f"{len(cases)} channels W~U{{64..256}} x 4W, 1 disk each", "cells": cells,
+                   "storage": args.precision, "l2": f"{cells * BYTES_PER_CELL[args.precision] / 2e6:.0f} MB of "
+                   "lattice state per step, larger than L2"},
+        "streams": {"value": round(mlups(streams_ms), 1), "unit": UNIT,
+                    "note": "each case on its own stream with vlb_step, issued one after another"},
+        "plain": {"value": round(mlups(plain_ms), 1), "unit": UNIT,
+                  "note": "one stream, one case after the other with vlb_step"},
+        "cases_per_s": round(len(cases) * args.steps / (batched_ms * 1e-3) / 5000.0, 2),
+        "cases_per_s_note": "cases of 5000 steps each",
+        "host_wall_mlups": round(cells * args.steps / host_s / 1e6, 1),
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle legs
 # ---------------------------------------------------------------------------
@@ -362,11 +463,15 @@ def main():
     ap.add_argument("--particles", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cavity", choices=["cavity", "channels"])
+    ap.add_argument("--cases", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "channels":
+        run_channels(args)
     else:
         run_ours(args)
 

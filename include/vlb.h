@@ -158,6 +158,27 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
  * earlier steps if one has been recorded. */
 vlb_status vlb_step(vlb_handle* h, int32_t nsteps);
 
+/* nsteps time steps of each of n handles (independent cases of any sizes,
+ * e.g. many small channels) with one launch of each kernel per step for all
+ * of them (one lattice launch per distinct precision / storage / held-path
+ * combination).  Each handle advances exactly as vlb_step(h, nsteps) would,
+ * bit for bit, and single steps and batch calls may alternate.  The work is
+ * queued on hs[0]'s stream after the work already queued on every handle's
+ * stream; every handle's stream then waits for it, so later calls on any
+ * handle are ordered after the batch.  Batch steps are not recorded by
+ * vlb_profile_begin / vlb_profile_end.
+ *   hs      host array of n distinct handles (borrowed)
+ *   failed  NULL, or receives -1 on success and else the index of the handle
+ *           whose failure is returned; vlb_last_error(hs[*failed]) describes
+ *           it (vlb_last_error(NULL) for a NULL handle or a bad argument).
+ * Errors: VLB_EINVAL for n < 0, nsteps < 0, a NULL or repeated handle; a
+ * handle's pending device flags (as vlb_step would return them); VLB_ECUDA.
+ * No handle advances unless every handle passes the checks.  Device flags
+ * raised during the call surface on each handle's next call, as with
+ * vlb_step.  Not part of the paper: it batches the paper's time step over
+ * cases. */
+vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed);
+
 /* Block until the handle's queued work is done; returns the first recorded
  * device-side failure, else VLB_OK. */
 vlb_status vlb_synchronize(vlb_handle* h);

@@ -65,6 +65,12 @@ struct vlb_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev;
   int ev_used = 0, ev_cap = 0;
+  cudaEvent_t join = nullptr;  // orders this handle's stream with a batch call's
+  // pinned staging of the descriptors of batch calls led by this handle, and
+  // the event after their last copy
+  unsigned char* bhost = nullptr;
+  size_t bhost_cap = 0;
+  cudaEvent_t bcopied = nullptr;
 };
 
 static thread_local std::string g_create_error;
@@ -188,6 +194,9 @@ static void free_all(vlb_handle* h) {
   if (h->err_host) cudaFreeHost(h->err_host);
   if (h->err_dev) cudaFree(h->err_dev);
   for (auto& e : h->ev) cudaEventDestroy(e);
+  if (h->join) cudaEventDestroy(h->join);
+  if (h->bcopied) cudaEventDestroy(h->bcopied);
+  if (h->bhost) cudaFreeHost(h->bhost);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -380,12 +389,12 @@ static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_b
 // Each band-kernel pass writes its entries with a new stamp (1 .. 2^29 - 1,
 // cycling); the lattice and dump kernels accept only entries with the stamp of
 // the tables they are given.
-static void next_band_stamp(vlb_handle* h) {
-  int s = h->PC.band_stamp + 1;
-  if (s >= (1 << 29)) s = 1;
+static void advance_band_stamp(vlb_handle* h, long long levels) {
+  const int s = band_stamp_after(h->PC.band_stamp, levels);
   h->PC.band_stamp = s;
   h->K32.band_stamp = h->K64.band_stamp = s;
 }
+static void next_band_stamp(vlb_handle* h) { advance_band_stamp(h, 1); }
 
 static vlb_status initialize(vlb_handle* h) {
   const vlb_params& p = h->p;
@@ -468,31 +477,236 @@ static vlb_status initialize(vlb_handle* h) {
   return VLB_OK;
 }
 
+// One time step of h, queued on its stream.
+static vlb_status step_once(vlb_handle* h) {
+  vlb_status s;
+  const int nl = 1 - h->tl;
+  CK(h, launch_particle_advance(h->PC, h->P, h->err_dev, h->stream));
+  next_band_stamp(h);
+  CK(h, launch_particle_band(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
+  const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
+  if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
+  if ((s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur, nl)) != VLB_OK) return s;
+  h->tl = nl;
+  if (rec) {
+    CK(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+    h->ev_used += 2;
+  }
+  h->cur = 1 - h->cur;
+  ++h->step;
+  h->macros_valid = false;
+  return VLB_OK;
+}
+
 vlb_status vlb_step(vlb_handle* h, int32_t nsteps) {
   if (!h) return VLB_EINVAL;
   if (nsteps < 0) return fail(h, VLB_EINVAL, "nsteps < 0");
   vlb_status s = device_flags(h);
   if (s != VLB_OK) return s;
   if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
-  for (int k = 0; k < nsteps; ++k) {
-    const int nl = 1 - h->tl;
-    CK(h, launch_particle_advance(h->PC, h->P, h->err_dev, h->stream));
-    next_band_stamp(h);
-    CK(h, launch_particle_band(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
-    const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
-    if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
-    if ((s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur, nl)) != VLB_OK) return s;
-    h->tl = nl;
-    if (rec) {
-      CK(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
-      h->ev_used += 2;
-    }
-    h->cur = 1 - h->cur;
-    ++h->step;
-    h->macros_valid = false;
-  }
+  for (int k = 0; k < nsteps; ++k)
+    if ((s = step_once(h)) != VLB_OK) return s;
   CK(h, pull_flags(h));
   return VLB_OK;
+}
+
+}  // extern "C"
+
+// Descriptors of one batch call, packed into one host block and one device
+// copy: the particle descriptors, the (case, particle) items, and per group
+// of handles that share a lattice kernel (precision, storage, held path) the
+// lattice descriptors and the tile-to-case table.
+namespace {
+struct BatchGroup {
+  bool f64 = false, held = false;
+  int storage = 0;
+  std::vector<int> handles;  // indices into the call's handle array
+  size_t desc_off = 0, table_off = 0;
+  int ntiles = 0;
+};
+
+size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
+
+template <class C>
+void fill_lattice_desc(vlb_handle* h, const LatticeConst<C>& K, int tile0, BatchLattice<C>& d) {
+  d = BatchLattice<C>{};
+  d.K = K;
+  for (int b = 0; b < 2; ++b) {
+    d.B[b].src = h->pop[b];
+    d.B[b].dst = h->pop[1 - b];
+    d.B[b].s_src = h->spl[b];
+    d.B[b].s_dst = h->spl[1 - b];
+    d.B[b].macro = h->macro;
+    d.B[b].err = h->err_dev;
+    d.TL[b] = h->TL[b];
+    d.TL[b].next_count = h->TL[1 - b].count;
+  }
+  d.P = h->P;
+  d.tile0 = tile0;
+  d.cur = h->cur;
+  d.tl = h->tl;
+  d.stamp = h->PC.band_stamp;
+}
+}  // namespace
+
+extern "C" {
+
+vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed) {
+  if (failed) *failed = -1;
+  if (n < 0 || (n > 0 && !hs)) return fail(nullptr, VLB_EINVAL, "vlb_step_batch: n < 0 or no handle array");
+  if (nsteps < 0) return fail(nullptr, VLB_EINVAL, "vlb_step_batch: nsteps < 0");
+  auto bad = [&](int i, vlb_status s) {
+    if (failed) *failed = i;
+    return s;
+  };
+#define BCK(i, call)                                                              \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) return bad((i), cuda_fail(hs[(i)], e_, #call));        \
+  } while (0)
+  for (int i = 0; i < n; ++i) {
+    vlb_handle* h = hs[i];
+    if (!h) return bad(i, fail(nullptr, VLB_EINVAL, "vlb_step_batch: NULL handle"));
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == h) return bad(i, fail(h, VLB_EINVAL, "vlb_step_batch: a handle appears twice"));
+    vlb_status s = device_flags(h);
+    if (s != VLB_OK) return bad(i, s);
+    if (!h->initialized && (s = initialize(h)) != VLB_OK) return bad(i, s);
+    if (!h->join) {
+      cudaError_t e = cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming);
+      if (e != cudaSuccess) return bad(i, cuda_fail(h, e, "event"));
+    }
+  }
+  if (n == 0 || nsteps == 0) {
+    for (int i = 0; i < n; ++i) {
+      cudaError_t e = pull_flags(hs[i]);
+      if (e != cudaSuccess) return bad(i, cuda_fail(hs[i], e, "pull_flags"));
+    }
+    return VLB_OK;
+  }
+
+  // ---- descriptors -----------------------------------------------------------
+  std::vector<BatchGroup> groups;
+  std::vector<int2> items;
+  for (int i = 0; i < n; ++i) {
+    vlb_handle* h = hs[i];
+    const bool f64 = h->p.precision == VLB_FP64;
+    const bool held = f64 ? h->K64.any_held : h->K32.any_held;
+    const int storage = f64 ? 0 : h->storage;
+    BatchGroup* g = nullptr;
+    for (auto& q : groups)
+      if (q.f64 == f64 && q.held == held && q.storage == storage) g = &q;
+    if (!g) {
+      groups.emplace_back();
+      g = &groups.back();
+      g->f64 = f64;
+      g->held = held;
+      g->storage = storage;
+    }
+    g->handles.push_back(i);
+    for (int k = 0; k < h->np; ++k) items.push_back(make_int2(i, k));
+  }
+  size_t bytes = align16(sizeof(BatchParticles) * n);
+  const size_t items_off = bytes;
+  bytes = align16(bytes + sizeof(int2) * items.size());
+  for (auto& g : groups) {
+    long long nt = 0;
+    for (int i : g.handles) nt += (long long)hs[i]->ntx * hs[i]->nty;
+    if (nt > (1ll << 31) - 1) return bad(g.handles[0], fail(hs[g.handles[0]], VLB_EINVAL, "vlb_step_batch: too many tiles"));
+    g.ntiles = (int)nt;
+    g.desc_off = bytes;
+    bytes = align16(bytes + (g.f64 ? sizeof(BatchLattice<double>) : sizeof(BatchLattice<float>)) * g.handles.size());
+    g.table_off = bytes;
+    bytes = align16(bytes + sizeof(int) * nt);
+  }
+  // the staging block of the previous call led by hs[0] is free once its copy ran
+  vlb_handle* h0 = hs[0];
+  if (!h0->bcopied) BCK(0, cudaEventCreateWithFlags(&h0->bcopied, cudaEventDisableTiming));
+  BCK(0, cudaEventSynchronize(h0->bcopied));
+  if (h0->bhost_cap < bytes) {
+    if (h0->bhost) cudaFreeHost(h0->bhost);
+    h0->bhost = nullptr;
+    h0->bhost_cap = 0;
+    BCK(0, cudaMallocHost(reinterpret_cast<void**>(&h0->bhost), bytes));
+    h0->bhost_cap = bytes;
+  }
+  unsigned char* hostp = h0->bhost;
+  std::memset(hostp, 0, bytes);
+  auto* bp = reinterpret_cast<BatchParticles*>(hostp);
+  for (int i = 0; i < n; ++i) {
+    vlb_handle* h = hs[i];
+    BatchParticles d{};
+    d.c = h->PC;
+    d.P = h->P;
+    d.TL[0] = h->TL[0];
+    d.TL[1] = h->TL[1];
+    d.err = h->err_dev;
+    d.tl = h->tl;
+    d.stamp = h->PC.band_stamp;
+    bp[i] = d;
+  }
+  if (!items.empty()) std::memcpy(hostp + items_off, items.data(), sizeof(int2) * items.size());
+  for (auto& g : groups) {
+    int* table = reinterpret_cast<int*>(hostp + g.table_off);
+    int tile0 = 0;
+    for (size_t c = 0; c < g.handles.size(); ++c) {
+      vlb_handle* h = hs[g.handles[c]];
+      if (g.f64) fill_lattice_desc(h, h->K64, tile0, reinterpret_cast<BatchLattice<double>*>(hostp + g.desc_off)[c]);
+      else fill_lattice_desc(h, h->K32, tile0, reinterpret_cast<BatchLattice<float>*>(hostp + g.desc_off)[c]);
+      const int nt = h->ntx * h->nty;
+      for (int t = 0; t < nt; ++t) table[tile0 + t] = (int)c;
+      tile0 += nt;
+    }
+  }
+
+  // ---- launches on the first handle's stream, joined with the others ---------
+  cudaStream_t bs = h0->stream;
+  for (int i = 1; i < n; ++i) {
+    vlb_handle* h = hs[i];
+    if (h->stream == bs) continue;
+    BCK(i, cudaEventRecord(h->join, h->stream));
+    BCK(0, cudaStreamWaitEvent(bs, h->join, 0));
+  }
+  unsigned char* dev = nullptr;
+  BCK(0, cudaMallocAsync(reinterpret_cast<void**>(&dev), bytes, bs));
+  cudaError_t e = cudaMemcpyAsync(dev, hostp, bytes, cudaMemcpyHostToDevice, bs);
+  if (e == cudaSuccess) e = cudaEventRecord(h0->bcopied, bs);
+  const auto* d_part = reinterpret_cast<const BatchParticles*>(dev);
+  const auto* d_items = reinterpret_cast<const int2*>(dev + items_off);
+  const int nitems = (int)items.size();
+  for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+    e = launch_particle_advance_batch(d_part, d_items, nitems, bs);
+    if (e == cudaSuccess) e = launch_particle_band_batch(d_part, d_items, nitems, k, bs);
+    for (auto& g : groups) {
+      if (e != cudaSuccess) break;
+      const int* table = reinterpret_cast<const int*>(dev + g.table_off);
+      e = g.f64 ? launch_lattice_batch_f64(reinterpret_cast<const BatchLattice<double>*>(dev + g.desc_off), table,
+                                           g.ntiles, k, g.held, bs)
+                : launch_lattice_batch_f32(reinterpret_cast<const BatchLattice<float>*>(dev + g.desc_off), table,
+                                           g.ntiles, k, g.storage, g.held, bs);
+    }
+  }
+  const cudaError_t ef = cudaFreeAsync(dev, bs);
+  if (e != cudaSuccess) return bad(0, cuda_fail(h0, e, "batch kernels"));
+  if (ef != cudaSuccess) return bad(0, cuda_fail(h0, ef, "batch descriptors"));
+  BCK(0, cudaEventRecord(h0->join, bs));
+  for (int i = 0; i < n; ++i) {
+    vlb_handle* h = hs[i];
+    if (h->stream != bs) {
+      cudaError_t ew = cudaStreamWaitEvent(h->stream, h0->join, 0);
+      if (ew != cudaSuccess) return bad(i, cuda_fail(h, ew, "stream join"));
+    }
+    // the host's view of the levels, as nsteps single steps would leave it
+    h->cur ^= nsteps & 1;
+    h->tl ^= nsteps & 1;
+    advance_band_stamp(h, nsteps);
+    h->step += nsteps;
+    h->macros_valid = false;
+    cudaError_t ep = pull_flags(h);
+    if (ep != cudaSuccess) return bad(i, cuda_fail(h, ep, "pull_flags"));
+  }
+  return VLB_OK;
+#undef BCK
 }
 
 vlb_status vlb_synchronize(vlb_handle* h) {

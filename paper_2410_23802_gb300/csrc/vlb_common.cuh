@@ -54,6 +54,13 @@ enum : unsigned {
   ERR_BAND = 128u,  // a band cell whose table entry is not of the current level
 };
 
+// Band-table stamps run 1 .. 2^29 - 1 and then start again at 1 (0: none
+// yet); the stamp k >= 1 levels after stamp s.
+constexpr int BAND_STAMP_CYCLE = (1 << 29) - 1;
+__host__ __device__ __forceinline__ int band_stamp_after(int s, long long k) {
+  return 1 + (int)(((long long)s - 1 + k) % BAND_STAMP_CYCLE);
+}
+
 // Kernel modes of the lattice kernel.
 enum : int { MODE_INIT = 0, MODE_STEP = 1, MODE_MACROS = 2 };
 

@@ -16,6 +16,29 @@ struct ParticleConst {
   double inv_zeta;                           // 1 / zeta
 };
 
+// One case of a batched time step (vlb_step_batch): one launch of each kernel
+// advances every case of a batch by a level.  The descriptors are written once
+// per batch call; step k (0, 1, ...) of the call reads population buffer
+// cur ^ (k & 1) and list buffer tl ^ (k & 1), fills list buffer
+// 1 - (tl ^ (k & 1)), and stamps the band tables band_stamp_after(stamp, k + 1),
+// which is what the k-th single-case step from the same state would do.
+template <class C>
+struct BatchLattice {
+  LatticeConst<C> K;
+  StepBuffers B[2];  // B[b]: the level in population buffer b, the next one into 1 - b
+  TileLists TL[2];   // TL[l]: list buffer l; next_count = the counts of buffer 1 - l
+  ParticleArrays P;
+  int tile0;         // first tile of the case in the batched grid (tiles row by row)
+  int cur, tl, stamp;
+};
+struct BatchParticles {
+  ParticleConst c;
+  ParticleArrays P;
+  TileLists TL[2];
+  unsigned* err;
+  int tl, stamp;
+};
+
 // Storage of the populations of the FP32-arithmetic kernels.
 enum : int { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
 
@@ -39,6 +62,18 @@ cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays
                                     cudaStream_t st);
 cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
                                  cudaStream_t st);
+
+// Batched step k: particles are items (case, particle) of `cases`; lattice
+// tiles map to their case through tile_case.  `held`: the held-temperature
+// path (every case of the launch shares precision, storage and held).
+cudaError_t launch_particle_advance_batch(const BatchParticles* cases, const int2* items, int nitems,
+                                          cudaStream_t st);
+cudaError_t launch_particle_band_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
+                                       cudaStream_t st);
+cudaError_t launch_lattice_batch_f32(const BatchLattice<float>* cases, const int* tile_case, int ntiles, int k,
+                                     int storage, bool held, cudaStream_t st);
+cudaError_t launch_lattice_batch_f64(const BatchLattice<double>* cases, const int* tile_case, int ntiles, int k,
+                                     bool held, cudaStream_t st);
 
 // FP64 audits: out[0] = sum f, out[1] = sum eps, out[2] = sum g (block partials
 // in scratch[3 * nblocks], summed in block order).

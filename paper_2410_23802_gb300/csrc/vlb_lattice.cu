@@ -241,7 +241,7 @@ __device__ __forceinline__ void pull_direct(const LatticeConst<C>& K, const Step
 template <class S, class C, int MODE, bool HOLD>
 __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuffers& B, const ParticleArrays& P,
                                          const TileLists& TL, int tile_x, int tile_y, C (&f)[9], C (&g)[9],
-                                         const C s_old, TileShared<C>& sh) {
+                                         const C s_old, TileShared<C>& sh, int band_stamp) {
   const PartTile<C>* s_p = sh.p;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TILE_X + tx;
@@ -301,7 +301,7 @@ __device__ __forceinline__ int cell_body(const LatticeConst<C>& K, const StepBuf
   C ofs[MAX_OWNERS];
   C fs = C(0);
   if (active && np > 0)
-    fs = raster_cell<C>(tx, ty, x, y, np, s_p, P.band, K.band_off, K.band_stamp, nown, own, ocls, ofs, B.err);
+    fs = raster_cell<C>(tx, ty, x, y, np, s_p, P.band, K.band_off, band_stamp, nown, own, ocls, ofs, B.err);
   else {
 #pragma unroll
     for (int k = 0; k < MAX_OWNERS; ++k) { own[k] = -1; ocls[k] = 0; ofs[k] = C(0); }
@@ -552,7 +552,34 @@ lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArray
   __shared__ TileShared<C> sh;
   C f[9], g[9], s_old;
   pull_direct<S, C, MODE>(K, B, blockIdx.x, blockIdx.y, f, g, s_old);
-  cell_body<S, C, MODE, HOLD>(K, B, P, TL, blockIdx.x, blockIdx.y, f, g, s_old, sh);
+  cell_body<S, C, MODE, HOLD>(K, B, P, TL, blockIdx.x, blockIdx.y, f, g, s_old, sh, K.band_stamp);
+}
+
+// Step k of a batch call (vlb_step_batch) over the tiles of many cases, one
+// CTA per tile as above: the tile's case descriptor is copied to shared
+// memory, then the single-case code runs on it.
+template <class S, class C, bool HOLD>
+__global__ void __launch_bounds__(TILE_X * TILE_Y, sizeof(C) == 4 ? VLB_LATTICE_MIN_BLOCKS : 1)
+lattice_batch_kernel(const BatchLattice<C>* __restrict__ cases, const int* __restrict__ tile_case, int k) {
+  __shared__ TileShared<C> sh;
+  __shared__ BatchLattice<C> d;
+  static_assert(sizeof(BatchLattice<C>) % 4 == 0, "descriptor copied as words");
+  {
+    const int* src = reinterpret_cast<const int*>(cases + tile_case[blockIdx.x]);
+    int* dst = reinterpret_cast<int*>(&d);
+    for (int w = threadIdx.y * TILE_X + threadIdx.x; w < (int)(sizeof(d) / 4); w += TILE_X * TILE_Y)
+      dst[w] = src[w];
+  }
+  __syncthreads();
+  const int par = k & 1;
+  const StepBuffers& B = d.B[d.cur ^ par];
+  const TileLists& TL = d.TL[1 - (d.tl ^ par)];
+  const int t = blockIdx.x - d.tile0;
+  const int tile_y = t / d.K.ntx, tile_x = t - tile_y * d.K.ntx;
+  C f[9], g[9], s_old;
+  pull_direct<S, C, MODE_STEP>(d.K, B, tile_x, tile_y, f, g, s_old);
+  cell_body<S, C, MODE_STEP, HOLD>(d.K, B, d.P, TL, tile_x, tile_y, f, g, s_old, sh,
+                                   band_stamp_after(d.stamp, k + 1));
 }
 
 // Ownership of every cell at the current level, from the same raster code as
@@ -647,6 +674,27 @@ cudaError_t launch_lattice_f32(int mode, const LatticeConst<float>& K, const Ste
 cudaError_t launch_lattice_f64(int mode, const LatticeConst<double>& K, const StepBuffers& B,
                                const ParticleArrays& P, const TileLists& TL, cudaStream_t st) {
   return launch_mode<double, double>(mode, K, B, P, TL, st);
+}
+
+template <class S, class C>
+static cudaError_t launch_batch(const BatchLattice<C>* cases, const int* tile_case, int ntiles, int k, bool held,
+                                cudaStream_t st) {
+  if (ntiles == 0) return cudaSuccess;
+  const dim3 block(TILE_X, TILE_Y);
+  if (held) lattice_batch_kernel<S, C, true><<<(unsigned)ntiles, block, 0, st>>>(cases, tile_case, k);
+  else lattice_batch_kernel<S, C, false><<<(unsigned)ntiles, block, 0, st>>>(cases, tile_case, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_batch_f32(const BatchLattice<float>* cases, const int* tile_case, int ntiles, int k,
+                                     int storage, bool held, cudaStream_t st) {
+  if (storage == STORE_F16) return launch_batch<__half, float>(cases, tile_case, ntiles, k, held, st);
+  if (storage == STORE_BF16) return launch_batch<__nv_bfloat16, float>(cases, tile_case, ntiles, k, held, st);
+  return launch_batch<float, float>(cases, tile_case, ntiles, k, held, st);
+}
+cudaError_t launch_lattice_batch_f64(const BatchLattice<double>* cases, const int* tile_case, int ntiles, int k,
+                                     bool held, cudaStream_t st) {
+  return launch_batch<double, double>(cases, tile_case, ntiles, k, held, st);
 }
 
 }  // namespace vlb

@@ -73,11 +73,8 @@ __global__ void particle_range_kernel(const ParticleConst c, const ParticleArray
   write_record(P, p, P.x[p], P.y[p], P.r[p], P.ux[p], P.uy[p], P.om[p], float(P.lam_s[p]), float(P.T0[p]));
 }
 
-// One thread per particle: each FP64 instruction then serves 32 particles
-// (GB300's FP64 pipe is narrow, so this layout matters more than latency).
-__global__ void particle_advance_kernel(const ParticleConst c, const ParticleArrays P, unsigned* err) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= c.np) return;
+// Particle p's update (one thread).
+__device__ __forceinline__ void advance_one(const ParticleConst& c, const ParticleArrays& P, int p, unsigned* err) {
   const double X = P.x[p], Y = P.y[p], R = P.r[p];
   const double ux = P.ux[p], uy = P.uy[p], om = P.om[p];
   const double* kp = P.pk + 8 * p;  // 1/M, 1/I, M_in, I_in, body factor, wall factor
@@ -145,6 +142,24 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
   // (the band kernel that follows appends the particle to the tile lists)
 }
 
+// One thread per particle: each FP64 instruction then serves 32 particles
+// (GB300's FP64 pipe is narrow, so this layout matters more than latency).
+__global__ void particle_advance_kernel(const ParticleConst c, const ParticleArrays P, unsigned* err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= c.np) return;
+  advance_one(c, P, p, err);
+}
+
+// The same over the particles of many cases (vlb_step_batch).
+__global__ void particle_advance_batch_kernel(const BatchParticles* __restrict__ cases,
+                                              const int2* __restrict__ items, int nitems) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nitems) return;
+  const int2 it = items[i];
+  const BatchParticles& d = cases[it.x];
+  advance_one(d.c, d.P, it.y, d.err);
+}
+
 // Exact classes and areas (Sec. 2) of the cells whose centre lies in the band
 // |d - R| < 0.75 of a disk, i.e. the cells the lattice kernel's quick test
 // leaves open; one warp per particle.  The warp runs the quick test of the
@@ -157,7 +172,7 @@ __global__ void particle_advance_kernel(const ParticleConst c, const ParticleArr
 constexpr int BAND_WARPS = 4;    // particles per CTA
 constexpr int BAND_QUEUE = 256;  // queued band cells per warp before an evaluation pass
 
-__device__ __forceinline__ void band_evaluate(const ParticleConst& c, const ParticleArrays& P, int p,
+__device__ __forceinline__ void band_evaluate(const ParticleConst& c, const ParticleArrays& P, int p, int stamp,
                                               const RasterRec& rc, int bw, const int* queue, int nq, int lane) {
   for (int j = lane; j < nq; j += 32) {
     const int k = queue[j];
@@ -168,17 +183,14 @@ __device__ __forceinline__ void band_evaluate(const ParticleConst& c, const Part
     tile_geometry(rc, x0, y0, q);
     float f;
     const int cls = cell_fraction(x - x0, y - y0, q, f);
-    P.band[(long long)p * bw * bw + k] = make_int2(cls | (c.band_stamp << 2), __float_as_int(f));
+    P.band[(long long)p * bw * bw + k] = make_int2(cls | (stamp << 2), __float_as_int(f));
   }
 }
 
-__global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const ParticleConst c, const ParticleArrays P,
-                                                                        const TileLists TL, unsigned* err) {
-  __shared__ int s_queue[BAND_WARPS][BAND_QUEUE];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int p = blockIdx.x * BAND_WARPS + warp;
-  if (p >= c.np) return;  // the whole warp
-  int* queue = s_queue[warp];
+// Particle p's lists and band table (one warp; queue: BAND_QUEUE ints of
+// shared memory of this warp).
+__device__ __forceinline__ void band_one(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
+                                         unsigned* err, int p, int stamp, int* queue, int lane) {
   const RasterRec rc = P.rec[p];
   const int bw = 2 * c.band_off + 1;
   // append the particle to the lists of the tiles of its range, one lane per tile
@@ -249,14 +261,37 @@ __global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const Pa
       nq += __popc(m);
       if (nq > BAND_QUEUE - 32) {  // evaluate what is queued before it can overflow
         __syncwarp();
-        band_evaluate(c, P, p, rc, bw, queue, nq, lane);
+        band_evaluate(c, P, p, stamp, rc, bw, queue, nq, lane);
         __syncwarp();
         nq = 0;
       }
     }
   }
   __syncwarp();
-  band_evaluate(c, P, p, rc, bw, queue, nq, lane);
+  band_evaluate(c, P, p, stamp, rc, bw, queue, nq, lane);
+}
+
+__global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const ParticleConst c, const ParticleArrays P,
+                                                                        const TileLists TL, unsigned* err) {
+  __shared__ int s_queue[BAND_WARPS][BAND_QUEUE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * BAND_WARPS + warp;
+  if (p >= c.np) return;  // the whole warp
+  band_one(c, P, TL, err, p, c.band_stamp, s_queue[warp], lane);
+}
+
+// The same over the particles of many cases, step k of a batch call.
+__global__ void __launch_bounds__(32 * BAND_WARPS)
+    particle_band_batch_kernel(const BatchParticles* __restrict__ cases, const int2* __restrict__ items, int nitems,
+                               int k) {
+  __shared__ int s_queue[BAND_WARPS][BAND_QUEUE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * BAND_WARPS + warp;
+  if (i >= nitems) return;  // the whole warp
+  const int2 it = items[i];
+  const BatchParticles& d = cases[it.x];
+  const int nl = 1 - (d.tl ^ (k & 1));
+  band_one(d.c, d.P, d.TL[nl], d.err, it.y, band_stamp_after(d.stamp, k + 1), s_queue[warp], lane);
 }
 
 static inline dim3 pgrid(int n) { return dim3((unsigned)((n + 127) / 128)); }
@@ -277,6 +312,19 @@ cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P
                                  cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
   particle_band_kernel<<<(unsigned)((c.np + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(c, P, TL, err);
+  return cudaGetLastError();
+}
+cudaError_t launch_particle_advance_batch(const BatchParticles* cases, const int2* items, int nitems,
+                                          cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  particle_advance_batch_kernel<<<(unsigned)((nitems + 31) / 32), 32, 0, st>>>(cases, items, nitems);
+  return cudaGetLastError();
+}
+cudaError_t launch_particle_band_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
+                                       cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  particle_band_batch_kernel<<<(unsigned)((nitems + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(
+      cases, items, nitems, k);
   return cudaGetLastError();
 }
 }  // namespace vlb

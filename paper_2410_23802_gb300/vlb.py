@@ -77,6 +77,7 @@ def _load():
         "vlb_set_fixed_temperature": (ctypes.c_int, [h, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
         "vlb_add_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
         "vlb_step": (ctypes.c_int, [h, ctypes.c_int32]),
+        "vlb_step_batch": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
         "vlb_synchronize": (ctypes.c_int, [h]),
         "vlb_get_step": (ctypes.c_int, [h, P(ctypes.c_int64)]),
         "vlb_get_fields": (ctypes.c_int, [h, ctypes.c_uint32, d, d, d, d, d]),
@@ -153,6 +154,14 @@ def vlb_add_particles(h, xy, radius, T0, k_ratio=None, uv=None, omega=None):
 
 def vlb_step(h, nsteps: int = 1):
     _check(_lib.vlb_step(h, int(nsteps)), h)
+
+
+def vlb_step_batch(handles, nsteps: int = 1):
+    """nsteps steps of every handle in `handles`, interleaved on their streams."""
+    hs = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    failed = ctypes.c_int32(-1)
+    st = _lib.vlb_step_batch(hs, len(handles), int(nsteps), ctypes.byref(failed))
+    _check(st, handles[failed.value] if failed.value >= 0 else None)
 
 
 def vlb_synchronize(h):

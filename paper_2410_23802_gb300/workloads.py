@@ -168,3 +168,26 @@ def cavity(side: int = 2048, n: int = 2048, diameter: float = 16.0, seed: int = 
         k = [10.0 ** rng.uniform(-1.0, 1.0) for _ in range(n)]
     return Case(f"cavity {side}x{side}, {n} disks D={diameter:g}", params, xs, ys, [0.5 * diameter] * n,
                 [0.0] * n, k)
+
+
+def channels(n: int = 256, seed: int = 20241104, w_min: int = 64, w_max: int = 256,
+             precision: str = "fp32") -> list:
+    """n independent single-disk channels in the proportions of the channel
+    case: width W ~ U{w_min..w_max}, length 4 W, disk diameter D = W U[0.1, 0.25]
+    released at rest at (W/2, 3 W), rho_s/rho_f ~ U[1.1, 2.0], R_lambda =
+    10^U[-1, 1], R_cv = 1.5, tau_f = 0.8, Pr = 0.7, g = 1e-5, beta from Gr = 100
+    on the case's D, fluid T = 1, particle T = 0, adiabatic no-slip walls."""
+    rng = SplitMix64(seed)
+    nu = (0.8 - 0.5) / 3.0
+    out = []
+    for k in range(n):
+        w = w_min + int(rng.next_u64() % (w_max - w_min + 1))
+        D = w * rng.uniform(0.1, 0.25)
+        rho_r = rng.uniform(1.1, 2.0)
+        k_r = 10.0 ** rng.uniform(-1.0, 1.0)
+        params = dict(nx=w, ny=4 * w, tau_f=0.8, prandtl=0.7, rho_ratio=rho_r, cv_ratio=1.5, k_ratio_default=k_r,
+                      gravity=(0.0, -1e-5), beta=gr_beta(100.0, nu, 1e-5, 1.0, D), T_ref=1.0, T_fluid_init=1.0,
+                      thermal_wall=(0, 0, 0, 0), wall_T=(0.0, 0.0, 0.0, 0.0), thermal_rates_mode=0,
+                      precision=precision)
+        out.append(Case(f"channel {w}x{4 * w}, 1 disk D={D:.3f}", params, [w / 2.0], [3.0 * w], [D / 2.0], [0.0]))
+    return out

@@ -1,7 +1,7 @@
 """Test-only glue: the same seeded case fed to the CUDA path and the oracle."""
 import numpy as np
 
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}  # VLB_FP64, VLB_FP32, VLB_FP16_STORE, VLB_BF16_STORE
 
 
 def gpu_lattice(case, precision=None, max_particles=None, **over):
