@@ -275,6 +275,78 @@ const char* vlb_last_error(const vlb_handle* h);
 /* Free every resource of h (NULL is ignored). */
 void vlb_destroy(vlb_handle* h);
 
+/* Device bytes that a handle of parameters p allocates for n particles of
+ * the given radii (create, particles and first step; rows padded to 128 B,
+ * band tables sized by the largest radius).  VLB_EINVAL for inconsistent
+ * parameters, as vlb_create would return it. */
+vlb_status vlb_device_bytes(const vlb_params* p, int32_t n, const double* radius, uint64_t* bytes);
+
+/* ---- Served mode ----------------------------------------------------------
+ * Independent cases (each a vlb_params block, its particles and a number of
+ * steps) are submitted as they arrive.  Each vlb_serve_poll call is one
+ * round: queued cases are admitted first come first served while their
+ * vlb_device_bytes fit in the HBM budget (and under max_active), then every
+ * resident case advances by the same number of steps with one
+ * vlb_step_batch call (at most steps_per_round, and at most what the nearest
+ * case still needs), then the cases that have done their steps are read
+ * back (fields and particle state into host memory), freed, and their time
+ * to result recorded.  A case advances bit for bit as it would alone with
+ * vlb_step.  All resident cases run on the server's own CUDA stream.  One
+ * host thread per server.  Not part of the paper: it serves the paper's
+ * time step to a stream of cases. */
+typedef struct vlb_server vlb_server;
+
+typedef struct {
+  uint64_t hbm_budget;      /* device bytes for resident cases (0: half of the free device memory at creation) */
+  int32_t steps_per_round;  /* most steps between two admission points (0: 100) */
+  int32_t max_active;       /* most resident cases (0: no limit) */
+} vlb_serve_params;
+
+typedef enum { VLB_CASE_QUEUED = 0, VLB_CASE_ACTIVE = 1, VLB_CASE_DONE = 2, VLB_CASE_FAILED = 3 } vlb_case_state;
+
+/* Defaults: budget 0 (half of free memory), 100 steps per round, no limit on resident cases. */
+vlb_status vlb_serve_params_default(vlb_serve_params* sp);
+
+/* A server (no device memory yet beyond its stream).  VLB_EINVAL for
+ * negative fields, VLB_ENOMEM, VLB_ECUDA. */
+vlb_status vlb_serve_create(const vlb_serve_params* sp, vlb_server** out);
+
+/* Queue a case: parameters p (copied), n particles as in vlb_add_particles
+ * (xy[2n], radius[n], T0[n], k_ratio[n] or NULL; copied), nsteps time
+ * steps.  *id receives the case id.  VLB_EINVAL for bad arguments or
+ * parameters (n > p->max_particles included), VLB_ENOMEM when the case alone
+ * exceeds the HBM budget.  Disk placement errors surface at admission, as a
+ * failed case. */
+vlb_status vlb_serve_submit(vlb_server* s, const vlb_params* p, int32_t n, const double* xy, const double* radius,
+                            const double* T0, const double* k_ratio, int64_t nsteps, int64_t* id);
+
+/* One round (see above); afterwards the numbers of queued, resident and
+ * finished (done or failed, not yet taken) cases, each pointer may be NULL.
+ * A case whose step fails (VLB_EUNSTABLE, VLB_EOVERFLOW) becomes
+ * VLB_CASE_FAILED and the others go on; VLB_ECUDA ends the round with the
+ * server's error. */
+vlb_status vlb_serve_poll(vlb_server* s, int32_t* nqueued, int32_t* nactive, int32_t* ndone);
+
+/* State (vlb_case_state), lattice size, particle count and times (seconds
+ * since the server's creation: times[0] submitted, [1] admitted, [2]
+ * finished with its result in host memory) of a case not yet taken. */
+vlb_status vlb_serve_case_info(vlb_server* s, int64_t id, int32_t* state, int32_t* nx, int32_t* ny, int32_t* n,
+                               double* times);
+
+/* The result of a finished case, then forgotten: the five fields as
+ * vlb_get_fields writes them (nx*ny each, any may be NULL) and the particle
+ * state [n][9] = x, y, theta, ux, uy, omega, F_x, F_y, T (may be NULL).  A
+ * failed case returns its failure (vlb_serve_last_error describes it) and is
+ * forgotten too; VLB_ESTATE for a case still queued or running. */
+vlb_status vlb_serve_take(vlb_server* s, int64_t id, double* rho, double* ux, double* uy, double* T, double* fs,
+                          double* pstate);
+
+/* Description of the server's last failure (of a failed vlb_serve_create when s is NULL). */
+const char* vlb_serve_last_error(const vlb_server* s);
+
+/* Free the server and every resident case (NULL is ignored). */
+void vlb_serve_destroy(vlb_server* s);
+
 #ifdef __cplusplus
 }
 #endif

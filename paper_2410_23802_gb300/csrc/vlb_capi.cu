@@ -200,48 +200,106 @@ static void free_all(vlb_handle* h) {
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
+}  // extern "C"
+
+// The first inconsistency of a parameter block, or nullptr.
+static const char* params_error(const vlb_params& p) {
+  if (p.abi_version != VLB_ABI_VERSION) return "abi_version mismatch";
+  if (p.nx < 2 || p.ny < 2 || p.nx > (1 << 16) || p.ny > (1 << 16))
+    return "nx, ny must be in [2, 65536]";
+  if (!(p.tau_f > 0.5)) return "tau_f must exceed 1/2";
+  if (!(p.lambda_q_flow > 0.0) || !(p.s_e > 0.0 && p.s_e < 2.0) || !(p.prandtl > 0.0))
+    return "lambda_q_flow, s_e or prandtl out of range";
+  if (!(p.rho_ratio > 0.0) || !(p.cv_ratio > 0.0) || !(p.k_ratio_default > 0.0))
+    return "rho_ratio, cv_ratio, k_ratio_default must be positive";
+  if (!(p.contact_range > 0.0) || !(p.contact_eps_p > 0.0) || !(p.contact_eps_w > 0.0))
+    return "contact parameters must be positive";
+  if (p.precision < VLB_FP64 || p.precision > VLB_BF16_STORE)
+    return "precision must be a vlb_precision value";
+  if (p.max_particles < 0 || p.max_particles > (1 << 24)) return "max_particles";
+  if (p.thermal_rates_mode != 0 && p.thermal_rates_mode != 1)
+    return "thermal_rates_mode must be 0 or 1";
+  for (int k = 0; k < 2; ++k)
+    if (p.periodic[k] != 0 && p.periodic[k] != 1) return "periodic must be 0/1";
+  for (int w = 0; w < 4; ++w)
+    if (p.thermal_wall[w] != 0 && p.thermal_wall[w] != 1) return "thermal_wall";
+  return nullptr;
+}
+
+// Sizes and layout every handle of parameters p uses (rows padded to 128 B).
+struct Layout {
+  int pitch, ntx, nty;
+  long long plane;
+  size_t ssize, esize;
+};
+static Layout layout_of(const vlb_params& p) {
+  Layout L;
+  L.esize = p.precision == VLB_FP64 ? 8 : 4;
+  L.ssize = p.precision == VLB_FP64 ? 8 : (p.precision == VLB_FP32 ? 4 : 2);
+  const int align = 128 / (int)L.ssize;
+  L.pitch = (p.nx + align - 1) / align * align;
+  L.plane = (long long)L.pitch * p.ny;
+  L.ntx = (p.nx + TILE_X - 1) / TILE_X;
+  L.nty = (p.ny + TILE_Y - 1) / TILE_Y;
+  return L;
+}
+static size_t a256(size_t b) { return (b + 255) / 256 * 256; }
+// The particle block: 15 doubles, one int4, NBR_CAP + 2 ints, 8 doubles and
+// one raster record per particle, every sub-array on a 256-byte boundary.
+static size_t particle_block_bytes(size_t capn) {
+  return 15 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) + a256(capn * sizeof(int)) +
+         a256(capn * NBR_CAP * sizeof(int)) + a256(capn * sizeof(int)) + a256(capn * 8 * sizeof(double)) +
+         a256(capn * sizeof(RasterRec));
+}
+static int band_offset(double rmax) { return (int)std::ceil(rmax) + 2; }
+constexpr int AUDIT_BLOCKS = 608;  // 4 x 152 SMs
+
+extern "C" {
+
+vlb_status vlb_device_bytes(const vlb_params* pp, int32_t n, const double* radius, uint64_t* bytes) {
+  if (!pp || !bytes || n < 0 || (n > 0 && !radius)) return fail(nullptr, VLB_EINVAL, "vlb_device_bytes: arguments");
+  if (const char* m = params_error(*pp)) return fail(nullptr, VLB_EINVAL, m);
+  const vlb_params& p = *pp;
+  const Layout L = layout_of(p);
+  double rmax = 0.0;
+  for (int k = 0; k < n; ++k) rmax = std::max(rmax, radius[k]);
+  const size_t ntiles = (size_t)L.ntx * L.nty;
+  const size_t bw = 2 * (size_t)band_offset(rmax) + 1;
+  uint64_t b = 0;
+  b += 2 * (18 * (uint64_t)L.plane * L.ssize + (uint64_t)L.plane * L.esize);  // populations, S
+  b += 7 * (uint64_t)L.plane * L.esize;                                       // macroscopic planes
+  b += 2 * ntiles * (sizeof(int) + TILE_CAP * sizeof(int));                   // tile lists
+  b += particle_block_bytes((size_t)std::max(std::max(p.max_particles, n), 1));
+  b += (uint64_t)n * (6 * sizeof(unsigned long long) + bw * bw * sizeof(int2));  // exchange sums, band tables
+  b += (3 * AUDIT_BLOCKS + 3) * sizeof(double) + sizeof(unsigned);
+  *bytes = b;
+  return VLB_OK;
+}
+
 vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   if (!out) return fail(nullptr, VLB_EINVAL, "out is NULL");
   *out = nullptr;
   if (!pp) return fail(nullptr, VLB_EINVAL, "params is NULL");
   const vlb_params& p = *pp;
-  if (p.abi_version != VLB_ABI_VERSION) return fail(nullptr, VLB_EINVAL, "abi_version mismatch");
-  if (p.nx < 2 || p.ny < 2 || p.nx > (1 << 16) || p.ny > (1 << 16))
-    return fail(nullptr, VLB_EINVAL, "nx, ny must be in [2, 65536]");
-  if (!(p.tau_f > 0.5)) return fail(nullptr, VLB_EINVAL, "tau_f must exceed 1/2");
-  if (!(p.lambda_q_flow > 0.0) || !(p.s_e > 0.0 && p.s_e < 2.0) || !(p.prandtl > 0.0))
-    return fail(nullptr, VLB_EINVAL, "lambda_q_flow, s_e or prandtl out of range");
-  if (!(p.rho_ratio > 0.0) || !(p.cv_ratio > 0.0) || !(p.k_ratio_default > 0.0))
-    return fail(nullptr, VLB_EINVAL, "rho_ratio, cv_ratio, k_ratio_default must be positive");
-  if (!(p.contact_range > 0.0) || !(p.contact_eps_p > 0.0) || !(p.contact_eps_w > 0.0))
-    return fail(nullptr, VLB_EINVAL, "contact parameters must be positive");
-  if (p.precision < VLB_FP64 || p.precision > VLB_BF16_STORE)
-    return fail(nullptr, VLB_EINVAL, "precision must be a vlb_precision value");
-  if (p.max_particles < 0 || p.max_particles > (1 << 24)) return fail(nullptr, VLB_EINVAL, "max_particles");
-  if (p.thermal_rates_mode != 0 && p.thermal_rates_mode != 1)
-    return fail(nullptr, VLB_EINVAL, "thermal_rates_mode must be 0 or 1");
-  for (int k = 0; k < 2; ++k)
-    if (p.periodic[k] != 0 && p.periodic[k] != 1) return fail(nullptr, VLB_EINVAL, "periodic must be 0/1");
-  for (int w = 0; w < 4; ++w)
-    if (p.thermal_wall[w] != 0 && p.thermal_wall[w] != 1) return fail(nullptr, VLB_EINVAL, "thermal_wall");
+  if (const char* m = params_error(p)) return fail(nullptr, VLB_EINVAL, m);
 
   vlb_handle* h = new (std::nothrow) vlb_handle();
   if (!h) return fail(nullptr, VLB_ENOMEM, "host allocation");
   h->p = p;
   h->nx = p.nx;
   h->ny = p.ny;
-  h->esize = p.precision == VLB_FP64 ? 8 : 4;
-  h->ssize = p.precision == VLB_FP64 ? 8 : (p.precision == VLB_FP32 ? 4 : 2);
+  const Layout L = layout_of(p);
+  h->esize = L.esize;
+  h->ssize = L.ssize;
   h->storage = p.precision == VLB_FP16_STORE ? STORE_F16 : (p.precision == VLB_BF16_STORE ? STORE_BF16 : STORE_F32);
-  const int align = 128 / (int)h->ssize;
-  h->pitch = (p.nx + align - 1) / align * align;
-  h->plane = (long long)h->pitch * p.ny;
+  h->pitch = L.pitch;
+  h->plane = L.plane;
   if (h->plane >= (1ll << 31)) {
     delete h;
     return fail(nullptr, VLB_EINVAL, "lattice too large for 32-bit cell offsets");
   }
-  h->ntx = (p.nx + TILE_X - 1) / TILE_X;
-  h->nty = (p.ny + TILE_Y - 1) / TILE_Y;
+  h->ntx = L.ntx;
+  h->nty = L.nty;
   h->cap = p.max_particles;
   auto bail = [&](cudaError_t e, const char* where) {
     g_create_error = std::string(where) + ": " + cudaGetErrorString(e);
@@ -265,15 +323,9 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     if ((e = cudaMalloc(&h->TL[b].ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
     cudaMemsetAsync(h->TL[b].count, 0, ntiles * sizeof(int), h->stream);
   }
-  // particle arrays: 15 doubles, one int4, NBR_CAP + 2 ints, 8 doubles and
-  // one raster record per particle; every sub-array starts on a
-  // 256-byte boundary (int4 and record loads need 16-byte alignment)
+  // particle arrays (int4 and record loads need 16-byte alignment)
   const size_t capn = (size_t)std::max(h->cap, 1);
-  auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t pbytes = 15 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) +
-                        a256(capn * sizeof(int)) + a256(capn * NBR_CAP * sizeof(int)) +
-                        a256(capn * sizeof(int)) + a256(capn * 8 * sizeof(double)) +
-                        a256(capn * sizeof(RasterRec));
+  const size_t pbytes = particle_block_bytes(capn);
   if ((e = cudaMalloc(&h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
   h->pbytes = pbytes;
   {
@@ -290,7 +342,7 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     h->P.rec = reinterpret_cast<RasterRec*>(b);
   }
   cudaMemsetAsync(h->pbase, 0, pbytes, h->stream);
-  h->audit_blocks = 608;  // 4 x 152 SMs
+  h->audit_blocks = AUDIT_BLOCKS;
   if ((e = cudaMalloc(&h->audit_scratch, (3 * h->audit_blocks + 3) * sizeof(double))) != cudaSuccess)
     return bail(e, "audit");
   h->audit_out = h->audit_scratch + 3 * h->audit_blocks;
@@ -404,7 +456,7 @@ static vlb_status initialize(vlb_handle* h) {
   // holds every cell with |d - R| < 0.75 (the centre lies in [xi, xi + 1))
   double rmax = 0.0;
   for (double r : h->hr) rmax = std::max(rmax, r);
-  const int band_off = (int)std::ceil(rmax) + 2;
+  const int band_off = band_offset(rmax);
   if (n > 0) {
     // exchange accumulators: zero before the first (initial) lattice pass
     CK(h, cudaMalloc(&h->P.mes, (size_t)n * 6 * sizeof(unsigned long long)));

@@ -61,6 +61,13 @@ class VlbError(RuntimeError):
         self.status = status
 
 
+class vlb_serve_params(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("steps_per_round", ctypes.c_int32), ("max_active", ctypes.c_int32)]
+
+
+VLB_CASE_QUEUED, VLB_CASE_ACTIVE, VLB_CASE_DONE, VLB_CASE_FAILED = 0, 1, 2, 3
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run paper_2410_23802_gb300.build.build() "
@@ -96,6 +103,17 @@ def _load():
         "vlb_profile_end": (ctypes.c_int, [h, d, P(ctypes.c_int32), P(ctypes.c_int32)]),
         "vlb_last_error": (ctypes.c_char_p, [h]),
         "vlb_destroy": (None, [h]),
+        "vlb_device_bytes": (ctypes.c_int, [P(vlb_params), ctypes.c_int32, d, P(ctypes.c_uint64)]),
+        "vlb_serve_params_default": (ctypes.c_int, [P(vlb_serve_params)]),
+        "vlb_serve_create": (ctypes.c_int, [P(vlb_serve_params), P(ctypes.c_void_p)]),
+        "vlb_serve_submit": (ctypes.c_int, [h, P(vlb_params), ctypes.c_int32, d, d, d, d, ctypes.c_int64,
+                                            P(ctypes.c_int64)]),
+        "vlb_serve_poll": (ctypes.c_int, [h, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int32)]),
+        "vlb_serve_case_info": (ctypes.c_int, [h, ctypes.c_int64, P(ctypes.c_int32), P(ctypes.c_int32),
+                                               P(ctypes.c_int32), P(ctypes.c_int32), d]),
+        "vlb_serve_take": (ctypes.c_int, [h, ctypes.c_int64, d, d, d, d, d, d]),
+        "vlb_serve_last_error": (ctypes.c_char_p, [h]),
+        "vlb_serve_destroy": (None, [h]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -334,6 +352,80 @@ class Lattice:
 
     def close(self):
         vlb_destroy(self.h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def vlb_device_bytes(params: vlb_params, radius) -> int:
+    """Device bytes of a handle of these parameters with particles of these radii."""
+    radius = np.ascontiguousarray(radius, dtype=np.float64).reshape(-1)
+    out = ctypes.c_uint64()
+    _check(_lib.vlb_device_bytes(ctypes.byref(params), radius.shape[0], _ptr(radius) if radius.size else None,
+                                 ctypes.byref(out)))
+    return out.value
+
+
+class Server:
+    """Served mode (vlb_serve_*): cases are submitted as they arrive, admitted
+    by HBM budget, stepped together, and their results taken when done."""
+
+    def __init__(self, hbm_budget: int = 0, steps_per_round: int = 100, max_active: int = 0):
+        sp = vlb_serve_params()
+        _check(_lib.vlb_serve_params_default(ctypes.byref(sp)))
+        sp.hbm_budget, sp.steps_per_round, sp.max_active = int(hbm_budget), int(steps_per_round), int(max_active)
+        self.s = ctypes.c_void_p()
+        st = _lib.vlb_serve_create(ctypes.byref(sp), ctypes.byref(self.s))
+        if st != VLB_OK:
+            raise VlbError(st, (_lib.vlb_serve_last_error(None) or b"").decode())
+
+    def _check(self, st):
+        if st != VLB_OK:
+            raise VlbError(st, (_lib.vlb_serve_last_error(self.s) or b"").decode())
+
+    def submit(self, params: vlb_params, xy, radius, T0, nsteps: int, k_ratio=None) -> int:
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+        radius = np.ascontiguousarray(radius, dtype=np.float64).reshape(-1)
+        T0 = np.ascontiguousarray(T0, dtype=np.float64).reshape(-1)
+        k = None if k_ratio is None else np.ascontiguousarray(k_ratio, dtype=np.float64).reshape(-1)
+        cid = ctypes.c_int64()
+        self._check(_lib.vlb_serve_submit(self.s, ctypes.byref(params), radius.shape[0], _ptr(xy), _ptr(radius),
+                                          _ptr(T0), _ptr(k), int(nsteps), ctypes.byref(cid)))
+        return cid.value
+
+    def poll(self):
+        """One round; returns (queued, active, finished)."""
+        q, a, d = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(_lib.vlb_serve_poll(self.s, ctypes.byref(q), ctypes.byref(a), ctypes.byref(d)))
+        return q.value, a.value, d.value
+
+    def info(self, cid: int) -> dict:
+        st, nx, ny, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        t = np.zeros(3)
+        self._check(_lib.vlb_serve_case_info(self.s, int(cid), ctypes.byref(st), ctypes.byref(nx), ctypes.byref(ny),
+                                             ctypes.byref(n), _ptr(t)))
+        return {"state": st.value, "nx": nx.value, "ny": ny.value, "n": n.value, "t_submit": t[0],
+                "t_admit": t[1], "t_done": t[2]}
+
+    def take(self, cid: int):
+        """(fields dict as Lattice.fields() gives it, particle dict) of a finished case."""
+        i = self.info(cid)
+        nx, ny, n = i["nx"], i["ny"], i["n"]
+        f = {k: np.empty((ny, nx)) for k in ("rho", "ux", "uy", "T", "fs")}
+        ps = np.empty((max(n, 1), 9))
+        self._check(_lib.vlb_serve_take(self.s, int(cid), _ptr(f["rho"]), _ptr(f["ux"]), _ptr(f["uy"]), _ptr(f["T"]),
+                                        _ptr(f["fs"]), _ptr(ps)))
+        ps = ps[:n]
+        names = ("x", "y", "theta", "ux", "uy", "omega", "fx", "fy", "torque")
+        return f, {k: ps[:, j].copy() for j, k in enumerate(names)}
+
+    def close(self):
+        if self.s is not None and self.s.value:
+            _lib.vlb_serve_destroy(self.s)
+            self.s.value = None
 
     def __enter__(self):
         return self

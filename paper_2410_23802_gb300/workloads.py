@@ -191,3 +191,27 @@ def channels(n: int = 256, seed: int = 20241104, w_min: int = 64, w_max: int = 2
                       precision=precision)
         out.append(Case(f"channel {w}x{4 * w}, 1 disk D={D:.3f}", params, [w / 2.0], [3.0 * w], [D / 2.0], [0.0]))
     return out
+
+
+def served_cases(n: int = 200, seed: int = 20241105, steps: int = 2000, side_log2=(6.0, 10.0),
+                 max_particles_log2: float = 9.0, d_range=(8.0, 24.0), max_solid: float = 0.3) -> list:
+    """A stream of n sedimentation cases for the served mode: (gap, Case,
+    steps) with gap the time since the previous arrival in units of the mean
+    (exponential, i.e. Poisson arrivals at rate 1).  Each case is a cavity
+    (the cavity case's parameters) of side 2^U[6, 10] (rounded), holding
+    floor(2^U[0, 9]) disks of one diameter D ~ U[8, 24] (fewer where their
+    area would pass max_solid of the upper 60 %), half of the cases with FP32
+    populations and half with FP16 storage."""
+    rng = SplitMix64(seed)
+    out = []
+    for k in range(n):
+        gap = -math.log(1.0 - rng.uniform())
+        side = int(round(2.0 ** rng.uniform(*side_log2)))
+        npart = int(2.0 ** rng.uniform(0.0, max_particles_log2))
+        D = rng.uniform(*d_range)
+        cap = int(max_solid * 0.6 * side * side / (math.pi * D * D / 4.0))
+        npart = max(1, min(npart, cap))
+        precision = "fp32" if rng.next_u64() & 1 else "fp16"
+        c = cavity(side=side, n=npart, diameter=D, seed=seed + 7919 * (k + 1), precision=precision)
+        out.append((gap, c, steps))
+    return out
