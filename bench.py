@@ -347,7 +347,7 @@ def run_channels(args):
         "cases_per_s": round(len(cases) * args.steps / (batched_ms * 1e-3) / 5000.0, 2),
         "cases_per_s_note": "cases of 5000 steps each",
         "host_wall_mlups": round(cells * args.steps / host_s / 1e6, 1),
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -409,7 +409,7 @@ def run_serve(args):
         return np.array(lat_s), span
 
     def served_run(rate):
-        arrive = np.cumsum(gaps) / rate
+        arrive = np.cumsum(gaps) / rate if rate else np.zeros(len(cases))  # None: all at once
         # the server's clock starts a little after `start`: times to result
         # below count from the arrival and may be overstated by that much
         start = time.perf_counter()
@@ -457,6 +457,11 @@ def run_serve(args):
                       "p99_ms": round(1e3 * float(np.percentile(lp, 99)), 2),
                       "cases_per_s": round(len(cases) / span_p, 2), "mlups": round(work / span_p / 1e6, 1)},
         }
+    ls, span = served_run(None)
+    res["all_at_once"] = {"served": {"p50_ms": round(1e3 * float(np.percentile(ls, 50)), 2),
+                                     "p99_ms": round(1e3 * float(np.percentile(ls, 99)), 2),
+                                     "cases_per_s": round(len(cases) / span, 2),
+                                     "mlups": round(work / span / 1e6, 1)}}
     hi = res["1.2"]["served"]
     line = {
         "metric": "served p50/p99 time to result (ms) and aggregate MLUPS",

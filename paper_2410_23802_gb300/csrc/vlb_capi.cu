@@ -2,10 +2,11 @@
 // the order of the kernels within a time step, and the copies to the host.
 //
 // One time step n -> n+1 on the handle's stream:
-//   particle_advance   F_c^n from the exchange sums and contact forces of level
+//   particle_step      F_c^n from the exchange sums and contact forces of level
 //                      n (clearing the sums), forward Euler to X^{n+1}, U^{n+1};
-//                      writes the raster records and appends each particle to
-//                      the tile lists of X^{n+1} (list buffer b)
+//                      writes the raster records, appends each particle to
+//                      the tile lists of X^{n+1} (list buffer b) and fills the
+//                      band tables of level n+1
 //   lattice (STEP)     fused pull / correction / thermal / collision pass that
 //                      writes level n+1, adds the exchange sums of level n+1,
 //                      lists the contact partners of level n+1, and clears list
@@ -533,9 +534,8 @@ static vlb_status initialize(vlb_handle* h) {
 static vlb_status step_once(vlb_handle* h) {
   vlb_status s;
   const int nl = 1 - h->tl;
-  CK(h, launch_particle_advance(h->PC, h->P, h->err_dev, h->stream));
   next_band_stamp(h);
-  CK(h, launch_particle_band(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
+  CK(h, launch_particle_step(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
   const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
   if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
   if ((s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur, nl)) != VLB_OK) return s;
@@ -727,8 +727,7 @@ vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int3
   const auto* d_items = reinterpret_cast<const int2*>(dev + items_off);
   const int nitems = (int)items.size();
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
-    e = launch_particle_advance_batch(d_part, d_items, nitems, bs);
-    if (e == cudaSuccess) e = launch_particle_band_batch(d_part, d_items, nitems, k, bs);
+    e = launch_particle_step_batch(d_part, d_items, nitems, k, bs);
     for (auto& g : groups) {
       if (e != cudaSuccess) break;
       const int* table = reinterpret_cast<const int*>(dev + g.table_off);
@@ -1093,8 +1092,8 @@ vlb_status vlb_profile_end(vlb_handle* h, double* lattice_ms, int32_t* lattice_l
   }
   if (lattice_ms) *lattice_ms = tot;
   if (lattice_launches) *lattice_launches = h->ev_used / 2;
-  // particle_advance (with binning) and the lattice kernel
-  if (launches_per_step) *launches_per_step = h->np > 0 ? 3 : 1;
+  // particle_step and the lattice kernel
+  if (launches_per_step) *launches_per_step = h->np > 0 ? 2 : 1;
   h->prof = false;
   h->ev_used = 0;
   return VLB_OK;

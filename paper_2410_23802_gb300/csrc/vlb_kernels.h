@@ -58,18 +58,19 @@ cudaError_t launch_raster_dump_f64(const LatticeConst<double>& K, const Particle
 // Particle step pieces.
 cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& P, unsigned* err,
                                   cudaStream_t st);
-cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, unsigned* err,
-                                    cudaStream_t st);
 cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
                                  cudaStream_t st);
 
-// Batched step k: particles are items (case, particle) of `cases`; lattice
-// tiles map to their case through tile_case.  `held`: the held-temperature
-// path (every case of the launch shares precision, storage and held).
-cudaError_t launch_particle_advance_batch(const BatchParticles* cases, const int2* items, int nitems,
-                                          cudaStream_t st);
-cudaError_t launch_particle_band_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
+// Advance and band pass of every particle in one launch (list buffer TL, the
+// stamp of ParticleConst).
+cudaError_t launch_particle_step(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
+                                 cudaStream_t st);
+cudaError_t launch_particle_step_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
                                        cudaStream_t st);
+
+// Batched step k: lattice tiles map to their case through tile_case.
+// `held`: the held-temperature path (every case of the launch shares
+// precision, storage and held).
 cudaError_t launch_lattice_batch_f32(const BatchLattice<float>* cases, const int* tile_case, int ntiles, int k,
                                      int storage, bool held, cudaStream_t st);
 cudaError_t launch_lattice_batch_f64(const BatchLattice<double>* cases, const int* tile_case, int ntiles, int k,

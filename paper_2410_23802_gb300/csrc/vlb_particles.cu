@@ -1,14 +1,15 @@
 // Particle kernels (Sec. 2.3).
 //
-//   particle_advance (one thread per particle, FP64): F_MES, T_MES of Eq. 28
-//     from the integer accumulators the lattice kernel filled (then cleared);
-//     the inside-fluid force and torque of Eq. 29 with backward differences;
-//     the short-range contact force; Eqs. 26 and 30 by forward Euler; the
-//     raster record and the tile range of the new position.
-//   particle_range: record and tile range of the initial state.
-//   particle_band (one warp per particle, FP32): appends the particle to the
-//     tile lists of its range (the lattice kernel sorts each list by id and
-//     finds the contact partners of the level) and fills its band table.
+//   particle_step (one launch per time step): for each particle
+//     advance (one lane, FP64): F_MES, T_MES of Eq. 28 from the integer
+//       accumulators the lattice kernel filled (then cleared); the
+//       inside-fluid force and torque of Eq. 29 with backward differences;
+//       the short-range contact force; Eqs. 26 and 30 by forward Euler; the
+//       raster record and the tile range of the new position;
+//     band pass (one warp, FP32): appends the particle to the tile lists of
+//       its range (the lattice kernel ranks each list by id and finds the
+//       contact partners of the level) and fills its band table.
+//   particle_range, particle_band: the same for the initial state.
 #include <math.h>
 
 #include "vlb_common.cuh"
@@ -142,24 +143,6 @@ __device__ __forceinline__ void advance_one(const ParticleConst& c, const Partic
   // (the band kernel that follows appends the particle to the tile lists)
 }
 
-// One thread per particle: each FP64 instruction then serves 32 particles
-// (GB300's FP64 pipe is narrow, so this layout matters more than latency).
-__global__ void particle_advance_kernel(const ParticleConst c, const ParticleArrays P, unsigned* err) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= c.np) return;
-  advance_one(c, P, p, err);
-}
-
-// The same over the particles of many cases (vlb_step_batch).
-__global__ void particle_advance_batch_kernel(const BatchParticles* __restrict__ cases,
-                                              const int2* __restrict__ items, int nitems) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nitems) return;
-  const int2 it = items[i];
-  const BatchParticles& d = cases[it.x];
-  advance_one(d.c, d.P, it.y, d.err);
-}
-
 // Exact classes and areas (Sec. 2) of the cells whose centre lies in the band
 // |d - R| < 0.75 of a disk, i.e. the cells the lattice kernel's quick test
 // leaves open; one warp per particle.  The warp runs the quick test of the
@@ -280,13 +263,39 @@ __global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const Pa
   band_one(c, P, TL, err, p, c.band_stamp, s_queue[warp], lane);
 }
 
-// The same over the particles of many cases, step k of a batch call.
-__global__ void __launch_bounds__(32 * BAND_WARPS)
-    particle_band_batch_kernel(const BatchParticles* __restrict__ cases, const int2* __restrict__ items, int nitems,
-                               int k) {
-  __shared__ int s_queue[BAND_WARPS][BAND_QUEUE];
+// One particle step (advance, then lists and band table) in one launch: the
+// two depend on the particle alone.  A CTA of STEP_WARPS warps takes
+// STEP_WARPS particles: warp 0 advances them, one lane each (so the FP64
+// instructions stay shared by many particles), then each warp runs the band
+// pass of one of them; the barrier between makes the new records visible.
+constexpr int STEP_WARPS = 16;
+
+__global__ void __launch_bounds__(32 * STEP_WARPS, 1) particle_step_kernel(const ParticleConst c, const ParticleArrays P,
+                                                                        const TileLists TL, unsigned* err) {
+  __shared__ int s_queue[STEP_WARPS][BAND_QUEUE];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * BAND_WARPS + warp;
+  const int p0 = blockIdx.x * STEP_WARPS;
+  if (warp == 0 && lane < STEP_WARPS && p0 + lane < c.np) advance_one(c, P, p0 + lane, err);
+  __syncthreads();
+  const int p = p0 + warp;
+  if (p >= c.np) return;  // the whole warp
+  band_one(c, P, TL, err, p, c.band_stamp, s_queue[warp], lane);
+}
+
+// The same over the particles of many cases, step k of a batch call.
+__global__ void __launch_bounds__(32 * STEP_WARPS, 1)
+    particle_step_batch_kernel(const BatchParticles* __restrict__ cases, const int2* __restrict__ items, int nitems,
+                               int k) {
+  __shared__ int s_queue[STEP_WARPS][BAND_QUEUE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * STEP_WARPS;
+  if (warp == 0 && lane < STEP_WARPS && i0 + lane < nitems) {
+    const int2 it = items[i0 + lane];
+    const BatchParticles& d = cases[it.x];
+    advance_one(d.c, d.P, it.y, d.err);
+  }
+  __syncthreads();
+  const int i = i0 + warp;
   if (i >= nitems) return;  // the whole warp
   const int2 it = items[i];
   const BatchParticles& d = cases[it.x];
@@ -302,28 +311,22 @@ cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& 
   particle_range_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, err);
   return cudaGetLastError();
 }
-cudaError_t launch_particle_advance(const ParticleConst& c, const ParticleArrays& P, unsigned* err,
-                                    cudaStream_t st) {
-  if (c.np == 0) return cudaSuccess;
-  particle_advance_kernel<<<(unsigned)((c.np + 31) / 32), 32, 0, st>>>(c, P, err);
-  return cudaGetLastError();
-}
 cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
                                  cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
   particle_band_kernel<<<(unsigned)((c.np + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(c, P, TL, err);
   return cudaGetLastError();
 }
-cudaError_t launch_particle_advance_batch(const BatchParticles* cases, const int2* items, int nitems,
-                                          cudaStream_t st) {
-  if (nitems == 0) return cudaSuccess;
-  particle_advance_batch_kernel<<<(unsigned)((nitems + 31) / 32), 32, 0, st>>>(cases, items, nitems);
+cudaError_t launch_particle_step(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
+                                 cudaStream_t st) {
+  if (c.np == 0) return cudaSuccess;
+  particle_step_kernel<<<(unsigned)((c.np + STEP_WARPS - 1) / STEP_WARPS), 32 * STEP_WARPS, 0, st>>>(c, P, TL, err);
   return cudaGetLastError();
 }
-cudaError_t launch_particle_band_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
+cudaError_t launch_particle_step_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
                                        cudaStream_t st) {
   if (nitems == 0) return cudaSuccess;
-  particle_band_batch_kernel<<<(unsigned)((nitems + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(
+  particle_step_batch_kernel<<<(unsigned)((nitems + STEP_WARPS - 1) / STEP_WARPS), 32 * STEP_WARPS, 0, st>>>(
       cases, items, nitems, k);
   return cudaGetLastError();
 }
