@@ -8,6 +8,7 @@ driver (and no GPU until the first CUDA call).
 from __future__ import annotations
 
 import concurrent.futures
+import json
 import os
 import shutil
 import subprocess
@@ -38,16 +39,37 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile (if needed) and return the path of libvlb.so.
+TUNED = os.path.join(PKG, "tuned.json")
 
-    Extra preprocessor definitions (tuning constants such as
-    VLB_LATTICE_MIN_BLOCKS=4) come from the environment variable VLB_DEFINES;
-    a change of them forces a rebuild."""
+
+def tuned_defines(path: str = TUNED) -> list[str]:
+    """The build-time shape the autotuner chose (``autotune.py``): the
+    ``defines`` of the entry named by ``use`` in tuned.json, else none."""
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        return list(rec[rec["use"]]["defines"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return []
+
+
+def build(verbose: bool = False, force: bool = False, defines: list[str] | None = None,
+          out: str | None = None) -> str:
+    """Compile (if needed) and return the path of the library.
+
+    Preprocessor definitions (tile height VLB_TILE_Y, VLB_LATTICE_MIN_BLOCKS)
+    come from `defines`, else from the environment variable VLB_DEFINES, else
+    from the autotuner's tuned.json; a change of them forces a rebuild.
+    `out` builds a library of another name (objects in a folder of its own)."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    defines = ["-D" + d for d in os.environ.get("VLB_DEFINES", "").split()]
-    stamp = os.path.join(BUILD, "defines.txt")
+    lib = out or LIB
+    bdir = BUILD if out is None else os.path.join(BUILD, os.path.splitext(os.path.basename(out))[0])
+    os.makedirs(bdir, exist_ok=True)
+    if defines is None:
+        env = os.environ.get("VLB_DEFINES")
+        defines = env.split() if env is not None else tuned_defines()
+    defines = ["-D" + d for d in defines]
+    stamp = os.path.join(bdir, "defines.txt")
     old = open(stamp).read() if os.path.exists(stamp) else ""
     if old != " ".join(defines):
         force = True
@@ -59,7 +81,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc, *ARCH, *FLAGS, *defines, "-I", os.path.join(ROOT, "include"), "-c", s, "-o", o])
@@ -73,11 +95,11 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

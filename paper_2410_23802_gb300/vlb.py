@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libvlb.so")
+LIB_PATH = os.environ.get("VLB_LIBRARY") or os.path.join(_HERE, "libvlb.so")  # another build (the autotuner's)
 
 VLB_ABI_VERSION = 1
 VLB_OK, VLB_EINVAL, VLB_ENOMEM, VLB_ECUDA, VLB_ESTATE, VLB_EUNSTABLE, VLB_EOVERFLOW, VLB_ETIMEOUT = (
