@@ -123,3 +123,35 @@ def test_device_bytes_match_the_allocation():
     used = free0 - free1
     # allocations are rounded up to 2 MiB pages (about 15 of them)
     assert est <= used + (4 << 20) and used <= est + (40 << 20), (est, used)
+
+
+def test_unstable_case_fails_alone():
+    """A case whose disk is driven past 0.5 lu per step (strong gravity: the
+    device sets its too-fast flag, no fault) ends as a failed case with
+    VLB_EUNSTABLE; the cases stepped in the same rounds finish and equal
+    their solo runs."""
+    from paper_2410_23802_gb300 import vlb as V
+    good = _stream()[:3]
+    c0 = W.channels(n=1, seed=5)[0]
+    prm = dict(c0.params, gravity=(0.0, -0.05), rho_ratio=3.0)
+    fast = dataclasses.replace(c0, params=prm)
+    with V.Server(steps_per_round=16) as srv:
+        ids = [_submit(srv, V, c, s) for c, s in good[:1]]
+        bad_id = _submit(srv, V, fast, 200)
+        ids += [_submit(srv, V, c, s) for c, s in good[1:]]
+        for _ in range(1000):
+            q, a, d = srv.poll()
+            if d == len(ids) + 1:
+                break
+        assert srv.info(bad_id)["state"] == V.VLB_CASE_FAILED
+        with pytest.raises(V.VlbError, match="EUNSTABLE"):
+            srv.take(bad_id)
+        results = [srv.take(i) for i in ids]
+    for (c, steps), (fs, ps) in zip(good, results):
+        with gpu_lattice(c) as lat:
+            lat.step(steps)
+            f, p = lat.fields(), lat.particles()
+        for name in f:
+            assert np.array_equal(f[name], fs[name], equal_nan=True), name
+        for name in ps:
+            assert np.array_equal(p[name], ps[name]), name
