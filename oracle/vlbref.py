@@ -883,3 +883,139 @@ def conjugate_erfc(x, t, X_i, T_h, T_c, lambda_f, R_lambda, R_cv):
     solid = T_h + (T_c - T_h) / (e + 1.0) * erfc((X_i - x) / (2.0 * math.sqrt(a_s * t)))
     fluid = T_c + (T_h - T_c) * e / (e + 1.0) * erfc((x - X_i) / (2.0 * math.sqrt(a_f * t)))
     return np.where(x < X_i, solid, fluid)
+
+
+# ---------------------------------------------------------------------------
+# The C ABI's entry points over the oracle: the names of include/vlb.h with
+# vlbref_ for vlb_, the same inputs in the same order and the same status
+# codes, so that one script can drive either side.  Outputs the C ABI writes
+# through caller-owned arrays are written into caller-owned numpy arrays of
+# the same layout (fields row-major with y slow; xy, uv, force interleaved);
+# out-scalars are returned after the status.
+# ---------------------------------------------------------------------------
+VLBREF_OK, VLBREF_EINVAL, VLBREF_ESTATE = 0, -1, -4
+VLBREF_FIELD_RHO, VLBREF_FIELD_UX, VLBREF_FIELD_UY, VLBREF_FIELD_T, VLBREF_FIELD_FS = 1, 2, 4, 8, 16
+
+
+class _RefHandle:
+    def __init__(self, prm: Params):
+        self.prm = prm
+        self.parts = {k: [] for k in ("x", "y", "r", "T0", "k", "ux", "uy", "omega", "fixed")}
+        self.sim = None
+        self.err = ""
+
+    def fail(self, status, msg):
+        self.err = msg
+        return status
+
+
+def vlbref_create(p: Params):
+    """(status, handle) for the problem p."""
+    if p.nx < 2 or p.ny < 2 or not p.tau_f > 0.5:
+        return VLBREF_EINVAL, None
+    return VLBREF_OK, _RefHandle(p)
+
+
+def vlbref_add_particles(h, n, xy, radius, T0, k_ratio=None, uv=None, omega=None):
+    """Disks before the first step: centres xy[2n], radii, initial
+    temperatures, optional conductivity ratios, velocities uv[2n], spins.
+    VLBREF_EINVAL for a disk outside the walls or overlapping another."""
+    if h.sim is not None:
+        return h.fail(VLBREF_ESTATE, "particles must be added before the first step")
+    xy = np.asarray(xy, dtype=float).reshape(-1)
+    P = h.parts
+    for k in range(n):
+        x, y, r = float(xy[2 * k]), float(xy[2 * k + 1]), float(radius[k])
+        if not (r > 0 and r <= x <= h.prm.nx - r and r <= y <= h.prm.ny - r):
+            return h.fail(VLBREF_EINVAL, "a disk lies outside the walls")
+        for x2, y2, r2 in zip(P["x"], P["y"], P["r"]):
+            if (x - x2) ** 2 + (y - y2) ** 2 < (r + r2) ** 2:
+                return h.fail(VLBREF_EINVAL, "particles overlap")
+        P["x"].append(x)
+        P["y"].append(y)
+        P["r"].append(r)
+        P["T0"].append(float(T0[k]))
+        P["k"].append(float(k_ratio[k]) if k_ratio is not None else h.prm.k_ratio_default)
+        P["ux"].append(float(uv[2 * k]) if uv is not None else 0.0)
+        P["uy"].append(float(uv[2 * k + 1]) if uv is not None else 0.0)
+        P["omega"].append(float(omega[k]) if omega is not None else 0.0)
+        P["fixed"].append(False)
+    return VLBREF_OK
+
+
+def vlbref_set_fixed_temperature(h, first, n, held):
+    """Hold particles first .. first + n - 1 at T0 (held[k] != 0), before the first step."""
+    if h.sim is not None:
+        return h.fail(VLBREF_ESTATE, "fixed temperatures must be set before the first step")
+    if first < 0 or n < 0 or first + n > len(h.parts["x"]):
+        return h.fail(VLBREF_EINVAL, "particle range")
+    for k in range(n):
+        h.parts["fixed"][first + k] = bool(held[k])
+    return VLBREF_OK
+
+
+def _ensure(h):
+    if h.sim is None:
+        P = h.parts
+        h.sim = Simulation(h.prm, P["x"], P["y"], P["r"], P["T0"], k_ratio=P["k"], ux=P["ux"], uy=P["uy"],
+                           omega=P["omega"], fixed_T=P["fixed"])
+
+
+def vlbref_step(h, nsteps):
+    """nsteps time steps (the initial state is built by the first call)."""
+    if nsteps < 0:
+        return h.fail(VLBREF_EINVAL, "nsteps < 0")
+    _ensure(h)
+    h.sim.step(nsteps)
+    return VLBREF_OK
+
+
+def vlbref_get_fields(h, mask, rho, ux, uy, T, fs):
+    """rho, u, T, f_s of the current level into the arrays whose bit is set in mask."""
+    _ensure(h)
+    f = h.sim.fields()
+    for bit, name, out in ((1, "rho", rho), (2, "ux", ux), (4, "uy", uy), (8, "T", T), (16, "fs", fs)):
+        if mask & bit:
+            if out is None:
+                return h.fail(VLBREF_EINVAL, "NULL field array for a selected field")
+            np.copyto(np.asarray(out).reshape(h.prm.ny, h.prm.nx), f[name])
+    return VLBREF_OK
+
+
+def vlbref_get_particle_count(h):
+    return VLBREF_OK, len(h.parts["x"])
+
+
+def vlbref_get_particle_state(h, n, xy, theta, uv, omega, force, torque):
+    """State of the first n particles: centres, angles, velocities, spins, F_c, T_c."""
+    _ensure(h)
+    s = h.sim.particle_state()
+    if n > len(s["x"]):
+        return h.fail(VLBREF_EINVAL, "n exceeds the particle count")
+    for out, parts in ((xy, ("x", "y")), (uv, ("ux", "uy")), (force, ("fx", "fy"))):
+        if out is not None:
+            o = np.asarray(out).reshape(-1)
+            o[0:2 * n:2], o[1:2 * n:2] = s[parts[0]][:n], s[parts[1]][:n]
+    for out, name in ((theta, "theta"), (omega, "omega"), (torque, "torque")):
+        if out is not None:
+            np.asarray(out).reshape(-1)[:n] = s[name][:n]
+    return VLBREF_OK
+
+
+def vlbref_get_audit(h):
+    """(status, total mass, total internal energy, sum g)."""
+    _ensure(h)
+    return (VLBREF_OK,) + tuple(h.sim.audit())
+
+
+def vlbref_get_step(h):
+    return VLBREF_OK, (h.sim.step_count if h.sim is not None else 0)
+
+
+def vlbref_last_error(h):
+    return h.err if h is not None else ""
+
+
+def vlbref_destroy(h):
+    if h is not None:
+        h.sim = None
