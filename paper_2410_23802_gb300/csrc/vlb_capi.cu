@@ -66,6 +66,7 @@ struct vlb_handle {
   bool prof = false;
   std::vector<cudaEvent_t> ev;
   int ev_used = 0, ev_cap = 0;
+  double* pstage = nullptr;    // pinned staging of particle-state read-backs [12][cap]
   cudaEvent_t join = nullptr;  // orders this handle's stream with a batch call's
   // pinned staging of the descriptors of batch calls led by this handle, and
   // the event after their last copy
@@ -196,6 +197,7 @@ static void free_all(vlb_handle* h) {
   if (h->err_dev) cudaFree(h->err_dev);
   for (auto& e : h->ev) cudaEventDestroy(e);
   if (h->join) cudaEventDestroy(h->join);
+  if (h->pstage) cudaFreeHost(h->pstage);
   if (h->bcopied) cudaEventDestroy(h->bcopied);
   if (h->bhost) cudaFreeHost(h->bhost);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -833,27 +835,25 @@ vlb_status vlb_get_particle_state(vlb_handle* h, int32_t n, double* xy, double* 
     }
     return VLB_OK;
   }
+  // the twelve state arrays x, y, theta, ux, uy, om, the three previous
+  // velocities, fcx, fcy, tc follow one another in the particle block, one
+  // 256-byte-aligned sub-array each: one strided copy takes n of each
+  const size_t stride = a256((size_t)std::max(h->cap, 1) * sizeof(double));
+  if (!h->pstage) CK(h, cudaMallocHost(reinterpret_cast<void**>(&h->pstage), 12 * (size_t)std::max(h->cap, 1) * sizeof(double)));
+  CK(h, cudaMemcpy2DAsync(h->pstage, n * sizeof(double), h->P.x, stride, n * sizeof(double), 12,
+                          cudaMemcpyDeviceToHost, h->stream));
   CK(h, pull_flags(h));
   CK(h, cudaStreamSynchronize(h->stream));
-  std::vector<double> a(n), b(n);
-  auto get = [&](const double* d, std::vector<double>& v) {
-    return cudaMemcpy(v.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost);
-  };
-  if (xy) {
-    CK(h, get(h->P.x, a)); CK(h, get(h->P.y, b));
-    for (int k = 0; k < n; ++k) { xy[2 * k] = a[k]; xy[2 * k + 1] = b[k]; }
+  const double* row[12];
+  for (int r = 0; r < 12; ++r) row[r] = h->pstage + (size_t)r * n;
+  for (int k = 0; k < n; ++k) {
+    if (xy) { xy[2 * k] = row[0][k]; xy[2 * k + 1] = row[1][k]; }
+    if (theta) theta[k] = row[2][k];
+    if (uv) { uv[2 * k] = row[3][k]; uv[2 * k + 1] = row[4][k]; }
+    if (omega) omega[k] = row[5][k];
+    if (force) { force[2 * k] = row[9][k]; force[2 * k + 1] = row[10][k]; }
+    if (torque) torque[k] = row[11][k];
   }
-  if (uv) {
-    CK(h, get(h->P.ux, a)); CK(h, get(h->P.uy, b));
-    for (int k = 0; k < n; ++k) { uv[2 * k] = a[k]; uv[2 * k + 1] = b[k]; }
-  }
-  if (force) {
-    CK(h, get(h->P.fcx, a)); CK(h, get(h->P.fcy, b));
-    for (int k = 0; k < n; ++k) { force[2 * k] = a[k]; force[2 * k + 1] = b[k]; }
-  }
-  if (theta) CK(h, cudaMemcpy(theta, h->P.theta, n * sizeof(double), cudaMemcpyDeviceToHost));
-  if (omega) CK(h, cudaMemcpy(omega, h->P.om, n * sizeof(double), cudaMemcpyDeviceToHost));
-  if (torque) CK(h, cudaMemcpy(torque, h->P.tc, n * sizeof(double), cudaMemcpyDeviceToHost));
   return device_flags(h);
 }
 
