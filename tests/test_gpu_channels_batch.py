@@ -132,3 +132,37 @@ def test_batch_argument_errors():
         assert V.vlb_get_step(a.h) == 0
         V.vlb_step_batch([b.h, a.h], 2)
         assert V.vlb_get_step(a.h) == V.vlb_get_step(b.h) == 2
+
+
+def test_channels_for_5000_steps():
+    """The whole configuration: 256 channels, 5000 steps each, batched.  No
+    case raises a device flag, every disk has settled (more than 1 lu down,
+    slower than 0.5 lu per step; a disk that reached the bottom may rebound
+    through the wall contact force), and the narrowest channel still matches
+    the oracle element by element after its first 500 steps (FP32 bar)."""
+    from paper_2410_23802_gb300 import vlb as V
+    cases = W.channels()
+    narrow = int(np.argmin([c.params["nx"] for c in cases]))
+    lats = [gpu_lattice(c) for c in cases]
+    try:
+        hs = [l.h for l in lats]
+        V.vlb_step_batch(hs, 500)
+        f500, p500 = lats[narrow].fields(), lats[narrow].particles()
+        V.vlb_step_batch(hs, 4500)
+        ps = []
+        for l in lats:
+            V.vlb_synchronize(l.h)  # raises on any device flag
+            assert V.vlb_get_step(l.h) == 5000
+            ps.append(l.particles())
+    finally:
+        for l in lats:
+            l.close()
+    for c, p in zip(cases, ps):
+        assert p["y"][0] < c.y[0] - 1.0
+        assert np.hypot(p["ux"][0], p["uy"][0]) < 0.5
+    sim = oracle_sim(cases[narrow])
+    sim.step(500)
+    ref, rp = sim.fields(), sim.particle_state()
+    assert rel_l2(np.stack([f500["ux"], f500["uy"]]), np.stack([ref["ux"], ref["uy"]])) < 1e-5
+    assert rel_l2(f500["T"], ref["T"]) < 1e-5
+    assert np.abs(p500["y"] - rp["y"]).max() < 1e-4
