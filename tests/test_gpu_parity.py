@@ -159,3 +159,18 @@ def test_full_size_cavity_first_steps():
     assert np.abs(got["fs"] - ref["fs"]).max() < 1e-5
     rp = sim.particle_state()
     assert np.abs(ps["y"] - rp["y"]).max() < 1e-9
+
+
+def test_partial_particle_state_read():
+    """vlb_get_particle_state for the first n of N particles returns exactly
+    their part of the full read (one strided copy of n elements per array)."""
+    from paper_2410_23802_gb300 import vlb as V
+    case = W.cavity(side=128, n=16, seed=11)
+    with gpu_lattice(case, max_particles=24) as lat:
+        lat.step(12)
+        full = V.vlb_get_particle_state(lat.h)
+        part = V.vlb_get_particle_state(lat.h, 5)
+        none = V.vlb_get_particle_state(lat.h, 0)
+    for k in full:
+        assert np.array_equal(part[k], full[k][:5]), k
+        assert none[k].shape == (0,)
