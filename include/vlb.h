@@ -284,13 +284,13 @@ vlb_status vlb_device_bytes(const vlb_params* p, int32_t n, const double* radius
 /* ---- Served mode ----------------------------------------------------------
  * Independent cases (each a vlb_params block, its particles and a number of
  * steps) are submitted as they arrive.  Each vlb_serve_poll call is one
- * round: queued cases are admitted first come first served while their
- * vlb_device_bytes fit in the HBM budget (and under max_active), then every
- * resident case advances by the same number of steps with one
+ * round: every resident case advances by the same number of steps with one
  * vlb_step_batch call (at most steps_per_round, and at most what the nearest
- * case still needs), then the cases that have done their steps are read
- * back (fields and particle state into host memory), freed, and their time
- * to result recorded.  A case advances bit for bit as it would alone with
+ * case still needs); while the GPU runs it, queued cases are admitted first
+ * come first served while their vlb_device_bytes fit in the HBM budget (and
+ * under max_active) and join the next round; then the cases that have done
+ * their steps are read back (fields and particle state into host memory),
+ * freed, and their time to result recorded.  A case advances bit for bit as it would alone with
  * vlb_step.  All resident cases run on the server's own CUDA stream.  One
  * host thread per server.  Not part of the paper: it serves the paper's
  * time step to a stream of cases. */

@@ -100,15 +100,17 @@ static void finish(vlb_server* s, ServeCase* c, vlb_status st, const char* msg) 
   std::vector<double>().swap(c->k_ratio);
 }
 
-// Create, fill and initialise the handle of a queued case.
+// Create, fill and initialise the handle of a queued case.  The initial
+// state is built on the handle's own stream, so that admission does not wait
+// for the round running on the server's stream; the handle then moves to it.
 static vlb_status admit(vlb_server* s, ServeCase* c) {
   vlb_status st = vlb_create(&c->p, &c->h);
   if (st != VLB_OK) return st;
-  st = vlb_set_stream(c->h, s->stream);
-  if (st == VLB_OK && c->n > 0)
+  if (c->n > 0)
     st = vlb_add_particles(c->h, c->n, c->xy.data(), c->radius.data(), c->T0.data(),
                            c->has_k ? c->k_ratio.data() : nullptr, nullptr, nullptr);
   if (st == VLB_OK) st = vlb_step(c->h, 0);  // initial state
+  if (st == VLB_OK) st = vlb_set_stream(c->h, s->stream);
   return st;
 }
 
@@ -174,24 +176,12 @@ vlb_status vlb_serve_submit(vlb_server* s, const vlb_params* p, int32_t n, const
 
 vlb_status vlb_serve_poll(vlb_server* s, int32_t* nqueued, int32_t* nactive, int32_t* ndone) {
   if (!s) return VLB_EINVAL;
-  // admission, first come first served, while the bytes fit
-  while (!s->queue.empty()) {
-    ServeCase* c = s->queue.front();
-    if (s->sp.max_active > 0 && (int)s->active.size() >= s->sp.max_active) break;
-    if (s->used + c->bytes > s->budget) break;
-    s->queue.pop_front();
-    s->used += c->bytes;
-    c->t_admit = s->now();
-    c->state = VLB_CASE_ACTIVE;
-    const vlb_status st = admit(s, c);
-    if (st != VLB_OK) finish(s, c, st, c->h ? vlb_last_error(c->h) : vlb_last_error(nullptr));
-    else if (c->nsteps == 0) finish(s, c, VLB_OK, nullptr);
-    else s->active.push_back(c);
-  }
-  // one round: every resident case advances by the same number of steps, at
-  // most steps_per_round and at most what the nearest case still needs
+  // 1. one round, queued on the server's stream: every resident case advances
+  //    by the same number of steps, at most steps_per_round and at most what
+  //    the nearest case still needs
+  int64_t chunk = 0;
   if (!s->active.empty()) {
-    int64_t chunk = s->sp.steps_per_round;
+    chunk = s->sp.steps_per_round;
     for (ServeCase* c : s->active) chunk = std::min(chunk, c->nsteps - c->done_steps);
     std::vector<vlb_handle*> hs;
     for (;;) {
@@ -207,16 +197,32 @@ vlb_status vlb_serve_poll(vlb_server* s, int32_t* nqueued, int32_t* nactive, int
       finish(s, c, st, vlb_last_error(c->h));
       if (s->active.empty()) break;
     }
-    if (!s->active.empty()) {
-      std::vector<ServeCase*> keep;
-      for (ServeCase* c : s->active) {
-        c->done_steps += chunk;
-        if (c->done_steps == c->nsteps) finish(s, c, VLB_OK, nullptr);
-        else keep.push_back(c);
-      }
-      s->active.swap(keep);
-    }
+    for (ServeCase* c : s->active) c->done_steps += chunk;
   }
+  // 2. admission while the round runs, first come first served, while the
+  //    bytes fit; the new cases join the next round
+  std::vector<ServeCase*> admitted;
+  while (!s->queue.empty()) {
+    ServeCase* c = s->queue.front();
+    if (s->sp.max_active > 0 && (int)(s->active.size() + admitted.size()) >= s->sp.max_active) break;
+    if (s->used + c->bytes > s->budget) break;
+    s->queue.pop_front();
+    s->used += c->bytes;
+    c->t_admit = s->now();
+    c->state = VLB_CASE_ACTIVE;
+    const vlb_status st = admit(s, c);
+    if (st != VLB_OK) finish(s, c, st, c->h ? vlb_last_error(c->h) : vlb_last_error(nullptr));
+    else if (c->nsteps == 0) finish(s, c, VLB_OK, nullptr);
+    else admitted.push_back(c);
+  }
+  // 3. the cases that have done their steps: results to host, then freed
+  std::vector<ServeCase*> keep;
+  for (ServeCase* c : s->active) {
+    if (c->done_steps == c->nsteps) finish(s, c, VLB_OK, nullptr);
+    else keep.push_back(c);
+  }
+  for (ServeCase* c : admitted) keep.push_back(c);
+  s->active.swap(keep);
   int32_t done = 0;
   for (auto& kv : s->cases)
     if (kv.second->state == VLB_CASE_DONE || kv.second->state == VLB_CASE_FAILED) ++done;
