@@ -363,10 +363,13 @@ def run_channels(args):
 
 
 def run_serve(args):
-    """Served mode against the plain path under the same seeded arrivals:
+    """Served mode (FP32 and FP16 storage, half each) against the plain
+    path (one case after the other, FP32) under the same seeded arrivals:
     Poisson arrivals at 0.8 and 1.2 times the plain path's measured service
     rate, time to result (arrival to fields and particle state in host
     memory) per case, aggregate MLUPS and cases/s over the makespan."""
+    import dataclasses
+
     import numpy as np
     import torch
     from paper_2410_23802_gb300 import vlb as V
@@ -387,7 +390,8 @@ def run_serve(args):
         return _params(c, V)
 
     def run_alone(c, n):
-        lat = V.Lattice(params(c))
+        """The plain path: one case on its own, FP32 populations."""
+        lat = V.Lattice(_params(dataclasses.replace(c, params=dict(c.params, precision="fp32")), V))
         V.vlb_set_stream(lat.h, stream_ptr)
         lat.add_particles(np.column_stack([c.x, c.y]), c.radius, c.T0, k_ratio=c.k_ratio)
         lat.step(n)
@@ -491,7 +495,8 @@ def run_serve(args):
         "loads": res,
         "clocks": clocks,
         "note": "value: aggregate MLUPS of the served run at 1.2x the plain service rate; "
-                "time to result = arrival to fields and particle state in host memory",
+                "time to result = arrival to fields and particle state in host memory; "
+                "plain: one case after the other with FP32 populations",
     }
     print(json.dumps(line), flush=True)
 
