@@ -200,6 +200,21 @@ vlb_status vlb_get_fields(vlb_handle* h, uint32_t mask, double* rho, double* ux,
 vlb_status vlb_get_particle_state(vlb_handle* h, int32_t n, double* xy, double* theta, double* uv,
                                   double* omega, double* force, double* torque);
 
+/* The same read without waiting for the GPU: vlb_particle_state_async queues
+ * a copy of the first n particles' state at the current level (after the
+ * work already queued on the handle's stream) into one of two
+ * library-owned pinned buffers and returns; vlb_particle_state_wait blocks
+ * until the oldest queued copy has arrived and writes it out like
+ * vlb_get_particle_state (any array may be NULL; n must equal the queued
+ * copy's), with the step number of its level in *step (may be NULL).  A
+ * caller that queues a copy after each vlb_step and collects it after the
+ * next one reads every step's result while the GPU runs the next step.
+ * VLB_ESTATE when two copies are pending (async) or none is (wait);
+ * VLB_EINVAL for a bad n; device flags as vlb_step returns them. */
+vlb_status vlb_particle_state_async(vlb_handle* h, int32_t n);
+vlb_status vlb_particle_state_wait(vlb_handle* h, int32_t n, double* xy, double* theta, double* uv, double* omega,
+                                   double* force, double* torque, int64_t* step);
+
 /* Number of particles in *n. */
 vlb_status vlb_get_particle_count(vlb_handle* h, int32_t* n);
 

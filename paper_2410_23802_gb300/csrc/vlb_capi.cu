@@ -67,6 +67,12 @@ struct vlb_handle {
   std::vector<cudaEvent_t> ev;
   int ev_used = 0, ev_cap = 0;
   double* pstage = nullptr;    // pinned staging of particle-state read-backs [12][cap]
+  // queued particle-state copies (vlb_particle_state_async): a ring of two
+  double* aring[2] = {nullptr, nullptr};
+  cudaEvent_t aev[2] = {nullptr, nullptr};
+  int an[2] = {0, 0};
+  long long astep[2] = {0, 0};
+  int ahead = 0, acount = 0;
   cudaEvent_t join = nullptr;  // orders this handle's stream with a batch call's
   // pinned staging of the descriptors of batch calls led by this handle, and
   // the event after their last copy
@@ -198,6 +204,10 @@ static void free_all(vlb_handle* h) {
   for (auto& e : h->ev) cudaEventDestroy(e);
   if (h->join) cudaEventDestroy(h->join);
   if (h->pstage) cudaFreeHost(h->pstage);
+  for (int b = 0; b < 2; ++b) {
+    if (h->aring[b]) cudaFreeHost(h->aring[b]);
+    if (h->aev[b]) cudaEventDestroy(h->aev[b]);
+  }
   if (h->bcopied) cudaEventDestroy(h->bcopied);
   if (h->bhost) cudaFreeHost(h->bhost);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -818,6 +828,26 @@ vlb_status vlb_get_particle_count(vlb_handle* h, int32_t* n) {
   return VLB_OK;
 }
 
+}  // extern "C"
+
+// The rows x, y, theta, ux, uy, om, (previous velocities), fcx, fcy, tc of a
+// staged particle-state copy [12][n] into the caller's arrays.
+static void unpack_particle_state(const double* st, int n, double* xy, double* theta, double* uv, double* omega,
+                                  double* force, double* torque) {
+  const double* row[12];
+  for (int r = 0; r < 12; ++r) row[r] = st + (size_t)r * n;
+  for (int k = 0; k < n; ++k) {
+    if (xy) { xy[2 * k] = row[0][k]; xy[2 * k + 1] = row[1][k]; }
+    if (theta) theta[k] = row[2][k];
+    if (uv) { uv[2 * k] = row[3][k]; uv[2 * k + 1] = row[4][k]; }
+    if (omega) omega[k] = row[5][k];
+    if (force) { force[2 * k] = row[9][k]; force[2 * k + 1] = row[10][k]; }
+    if (torque) torque[k] = row[11][k];
+  }
+}
+
+extern "C" {
+
 vlb_status vlb_get_particle_state(vlb_handle* h, int32_t n, double* xy, double* theta, double* uv,
                                   double* omega, double* force, double* torque) {
   if (!h) return VLB_EINVAL;
@@ -844,16 +874,43 @@ vlb_status vlb_get_particle_state(vlb_handle* h, int32_t n, double* xy, double* 
                           cudaMemcpyDeviceToHost, h->stream));
   CK(h, pull_flags(h));
   CK(h, cudaStreamSynchronize(h->stream));
-  const double* row[12];
-  for (int r = 0; r < 12; ++r) row[r] = h->pstage + (size_t)r * n;
-  for (int k = 0; k < n; ++k) {
-    if (xy) { xy[2 * k] = row[0][k]; xy[2 * k + 1] = row[1][k]; }
-    if (theta) theta[k] = row[2][k];
-    if (uv) { uv[2 * k] = row[3][k]; uv[2 * k + 1] = row[4][k]; }
-    if (omega) omega[k] = row[5][k];
-    if (force) { force[2 * k] = row[9][k]; force[2 * k + 1] = row[10][k]; }
-    if (torque) torque[k] = row[11][k];
-  }
+  unpack_particle_state(h->pstage, n, xy, theta, uv, omega, force, torque);
+  return device_flags(h);
+}
+
+vlb_status vlb_particle_state_async(vlb_handle* h, int32_t n) {
+  if (!h) return VLB_EINVAL;
+  if (n < 0 || n > h->np) return fail(h, VLB_EINVAL, "n exceeds the particle count");
+  if (h->acount == 2) return fail(h, VLB_ESTATE, "two particle-state copies are pending");
+  vlb_status st = device_flags(h);
+  if (st != VLB_OK) return st;
+  if (!h->initialized && (st = initialize(h)) != VLB_OK) return st;
+  const int b = (h->ahead + h->acount) % 2;
+  const size_t cap = (size_t)std::max(h->cap, 1);
+  if (!h->aring[b]) CK(h, cudaMallocHost(reinterpret_cast<void**>(&h->aring[b]), 12 * cap * sizeof(double)));
+  if (!h->aev[b]) CK(h, cudaEventCreateWithFlags(&h->aev[b], cudaEventDisableTiming));
+  if (n > 0)
+    CK(h, cudaMemcpy2DAsync(h->aring[b], n * sizeof(double), h->P.x, a256(cap * sizeof(double)), n * sizeof(double),
+                            12, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, pull_flags(h));
+  CK(h, cudaEventRecord(h->aev[b], h->stream));
+  h->an[b] = n;
+  h->astep[b] = h->step;
+  ++h->acount;
+  return VLB_OK;
+}
+
+vlb_status vlb_particle_state_wait(vlb_handle* h, int32_t n, double* xy, double* theta, double* uv, double* omega,
+                                   double* force, double* torque, int64_t* step) {
+  if (!h) return VLB_EINVAL;
+  if (h->acount == 0) return fail(h, VLB_ESTATE, "no particle-state copy is pending");
+  const int b = h->ahead;
+  if (n != h->an[b]) return fail(h, VLB_EINVAL, "n differs from the queued copy's");
+  CK(h, cudaEventSynchronize(h->aev[b]));
+  h->ahead = 1 - h->ahead;
+  --h->acount;
+  unpack_particle_state(h->aring[b], n, xy, theta, uv, omega, force, torque);
+  if (step) *step = h->astep[b];
   return device_flags(h);
 }
 

@@ -90,6 +90,8 @@ def _load():
         "vlb_get_fields": (ctypes.c_int, [h, ctypes.c_uint32, d, d, d, d, d]),
         "vlb_get_particle_state": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
         "vlb_get_particle_count": (ctypes.c_int, [h, P(ctypes.c_int32)]),
+        "vlb_particle_state_async": (ctypes.c_int, [h, ctypes.c_int32]),
+        "vlb_particle_state_wait": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d, P(ctypes.c_int64)]),
         "vlb_get_audit": (ctypes.c_int, [h, d, d, d]),
         "vlb_get_solid_fraction": (ctypes.c_int, [h, P(ctypes.c_uint8), P(ctypes.c_int32),
                                                   P(ctypes.c_uint8), d]),
@@ -224,6 +226,24 @@ def vlb_get_particle_state(h, n: int | None = None) -> dict:
     return {"x": xy[:, 0].copy(), "y": xy[:, 1].copy(), "theta": theta, "ux": uv[:, 0].copy(),
             "uy": uv[:, 1].copy(), "omega": omega, "fx": force[:, 0].copy(), "fy": force[:, 1].copy(),
             "torque": torque}
+
+
+def vlb_particle_state_async(h, n: int):
+    """Queue a copy of the first n particles' state at the current level (no wait)."""
+    _check(_lib.vlb_particle_state_async(h, int(n)), h)
+
+
+def vlb_particle_state_wait(h, n: int, out: dict | None = None) -> tuple[dict, int]:
+    """The oldest queued copy (as vlb_get_particle_state returns it) and its step.
+    `out` (a dict of arrays from an earlier call) is filled in place when given."""
+    if out is None:
+        out = {"xy": np.empty((n, 2)), "uv": np.empty((n, 2)), "force": np.empty((n, 2)),
+               "theta": np.empty(n), "omega": np.empty(n), "torque": np.empty(n)}
+    step = ctypes.c_int64()
+    _check(_lib.vlb_particle_state_wait(h, int(n), _ptr(out["xy"]), _ptr(out["theta"]), _ptr(out["uv"]),
+                                        _ptr(out["omega"]), _ptr(out["force"]), _ptr(out["torque"]),
+                                        ctypes.byref(step)), h)
+    return out, step.value
 
 
 def vlb_get_audit(h):

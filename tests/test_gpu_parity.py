@@ -174,3 +174,33 @@ def test_partial_particle_state_read():
     for k in full:
         assert np.array_equal(part[k], full[k][:5]), k
         assert none[k].shape == (0,)
+
+
+def test_async_particle_state_reads_every_step():
+    """Copies queued after each step and collected one step later equal the
+    synchronous reads of the same levels; the ring holds two copies."""
+    from paper_2410_23802_gb300 import vlb as V
+    case = W.cavity(side=128, n=16, seed=11)
+    sync = []
+    with gpu_lattice(case) as a:
+        for _ in range(6):
+            a.step(1)
+            sync.append(V.vlb_get_particle_state(a.h))
+    got = []
+    with gpu_lattice(case) as b:
+        with pytest.raises(V.VlbError, match="ESTATE"):
+            V.vlb_particle_state_wait(b.h, 16)
+        b.step(1)
+        V.vlb_particle_state_async(b.h, 16)
+        for k in range(1, 6):
+            b.step(1)
+            V.vlb_particle_state_async(b.h, 16)
+            with pytest.raises(V.VlbError, match="ESTATE"):  # a third copy
+                V.vlb_particle_state_async(b.h, 16)
+            got.append(V.vlb_particle_state_wait(b.h, 16))
+        got.append(V.vlb_particle_state_wait(b.h, 16))
+    for k, ((st, step), ref) in enumerate(zip(got, sync)):
+        assert step == k + 1
+        assert np.array_equal(st["xy"][:, 0], ref["x"]) and np.array_equal(st["xy"][:, 1], ref["y"])
+        assert np.array_equal(st["uv"][:, 1], ref["uy"]) and np.array_equal(st["omega"], ref["omega"])
+        assert np.array_equal(st["force"][:, 1], ref["fy"]) and np.array_equal(st["torque"], ref["torque"])
