@@ -281,7 +281,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:  # the host cores are timed at N = 1 only
         line["cpu_baseline"] = cpu_baseline(args, budget_s=15.0)
     print(json.dumps(line), flush=True)
 
