@@ -152,6 +152,23 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
                              const double* T0, const double* k_ratio, const double* uv,
                              const double* omega);
 
+/* Add n disks between two steps (mid-run insertion; before the first step
+ * the same as vlb_add_particles).  Reading (the paper has no insertion): a
+ * disk inserted at the current level n joins the particle set with the given
+ * centre and velocity and first appears in the solid fraction of level n+1;
+ * from there the paper's own equations act on it -- the volumetric
+ * correction (Eq. 8) imposes its velocity in the cells it covers, and the
+ * change of f_s enters the energy equation through df_s/dt (Eq. 24), so a
+ * conducting disk starts at the temperature of the fluid it displaces (T0
+ * is kept for vlb_set_fixed_temperature-style holding and inspection).  Its
+ * first update has no exchange or particle contact force.  Arguments as for
+ * vlb_add_particles.  Errors: VLB_EINVAL for a disk outside the domain,
+ * overlapping a disk where that disk is now, or larger than the largest disk
+ * present at the first step (the band tables' size); VLB_EOVERFLOW beyond
+ * max_particles.  Synchronises the handle's stream. */
+vlb_status vlb_insert_particles(vlb_handle* h, int32_t n, const double* xy, const double* radius, const double* T0,
+                                const double* k_ratio, const double* uv, const double* omega);
+
 /* Advance nsteps >= 0 time steps (asynchronous).  The first call builds the
  * initial state (f at rest, corrected by f_s^0; g at equilibrium with the
  * volume-weighted initial temperature).  Returns a device-side failure of

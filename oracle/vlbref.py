@@ -45,6 +45,11 @@ R6  Initial state: f* = f^eq(1, 0) corrected with f_s^0 (Eq. 8); the internal
     [df_s/dt]^0 = 0.
 R7  Domain: fractions exist only for cells inside the domain; a particle may
     not cross a periodic boundary.
+R12 Mid-run insertion (the paper has none): a disk added at level n joins the
+    particle set and first appears in the raster of level n+1; the correction
+    (Eq. 8) and the df_s/dt recursion (Eq. 24) then act on it as on a disk
+    moving into cells, so it starts at the temperature of the fluid it
+    displaces; its first update has no exchange and no contact force.
 """
 from __future__ import annotations
 
@@ -759,6 +764,36 @@ class Simulation:
         P["ux_prev"], P["uy_prev"], P["omega_prev"] = P["ux"], P["uy"], P["omega"]
         P["ux"], P["uy"], P["omega"] = ux_new, uy_new, om_new
 
+    def insert_particles(self, x, y, radius, T0, k_ratio=None, ux=None, uy=None, omega=None):
+        """Disks added at the current level (mid-run insertion; reading R12):
+        they join the particle set with the given centre and velocity and
+        first appear in the raster of the next level, where the correction
+        (Eq. 8) and the df_s/dt recursion (Eq. 24) act on them as on any disk
+        moving into cells; their first update has no exchange and no contact
+        force (neither was formed at this level)."""
+        n = len(x)
+        z = np.zeros(n)
+        P = self.part
+        new = {"x": x, "y": y, "r": radius, "T0": T0,
+               "k": k_ratio if k_ratio is not None else np.full(n, self.prm.k_ratio_default),
+               "ux": ux if ux is not None else z, "uy": uy if uy is not None else z,
+               "omega": omega if omega is not None else z, "theta": z}
+        for key, v in new.items():
+            P[key] = np.concatenate([P[key], np.asarray(v, dtype=float)])
+        P["ux_prev"] = np.concatenate([P["ux_prev"], np.asarray(new["ux"], dtype=float)])
+        P["uy_prev"] = np.concatenate([P["uy_prev"], np.asarray(new["uy"], dtype=float)])
+        P["omega_prev"] = np.concatenate([P["omega_prev"], np.asarray(new["omega"], dtype=float)])
+        r = P["r"]
+        self.mass = self.prm.rho_ratio * math.pi * r * r
+        self.inertia = 0.5 * self.mass * r * r
+        self.mass_in = 1.0 * math.pi * r * r
+        self.inertia_in = 0.5 * self.mass_in * r * r
+        self.fixed_T = np.concatenate([self.fixed_T, np.zeros(n, dtype=bool)])
+        self.F_mes = np.concatenate([self.F_mes, np.zeros((n, 2))])
+        self.T_mes = np.concatenate([self.T_mes, z])
+        self.Fc = np.concatenate([self.Fc, np.zeros((n, 2))])
+        self.Tc = np.concatenate([self.Tc, z])
+
     def step(self, nsteps: int = 1):
         for _ in range(nsteps):
             self._step()
@@ -959,6 +994,26 @@ def _ensure(h):
         P = h.parts
         h.sim = Simulation(h.prm, P["x"], P["y"], P["r"], P["T0"], k_ratio=P["k"], ux=P["ux"], uy=P["uy"],
                            omega=P["omega"], fixed_T=P["fixed"])
+
+
+def vlbref_insert_particles(h, n, xy, radius, T0, k_ratio=None, uv=None, omega=None):
+    """Disks between two steps (before the first one: vlbref_add_particles)."""
+    if h.sim is None:
+        return vlbref_add_particles(h, n, xy, radius, T0, k_ratio, uv, omega)
+    xy = np.asarray(xy, dtype=float).reshape(-1)
+    uv = None if uv is None else np.asarray(uv, dtype=float).reshape(-1)
+    P = h.sim.part
+    for k in range(n):
+        x, y, r = float(xy[2 * k]), float(xy[2 * k + 1]), float(radius[k])
+        if not (r > 0 and r <= x <= h.prm.nx - r and r <= y <= h.prm.ny - r):
+            return h.fail(VLBREF_EINVAL, "a disk lies outside the walls")
+        if ((P["x"] - x) ** 2 + (P["y"] - y) ** 2 < (P["r"] + r) ** 2).any():
+            return h.fail(VLBREF_EINVAL, "particles overlap")
+    h.sim.insert_particles(xy[0:2 * n:2], xy[1:2 * n:2], list(radius[:n]), list(T0[:n]),
+                           k_ratio=None if k_ratio is None else list(k_ratio[:n]),
+                           ux=None if uv is None else uv[0:2 * n:2], uy=None if uv is None else uv[1:2 * n:2],
+                           omega=None if omega is None else list(omega[:n]))
+    return VLBREF_OK
 
 
 def vlbref_step(h, nsteps):

@@ -283,7 +283,8 @@ vlb_status vlb_device_bytes(const vlb_params* pp, int32_t n, const double* radiu
   b += 7 * (uint64_t)L.plane * L.esize;                                       // macroscopic planes
   b += 2 * ntiles * (sizeof(int) + TILE_CAP * sizeof(int));                   // tile lists
   b += particle_block_bytes((size_t)std::max(std::max(p.max_particles, n), 1));
-  b += (uint64_t)n * (6 * sizeof(unsigned long long) + bw * bw * sizeof(int2));  // exchange sums, band tables
+  // exchange sums and band tables, sized for max_particles
+  b += (uint64_t)std::max(p.max_particles, n) * (6 * sizeof(unsigned long long) + bw * bw * sizeof(int2));
   b += (3 * AUDIT_BLOCKS + 3) * sizeof(double) + sizeof(unsigned);
   *bytes = b;
   return VLB_OK;
@@ -433,6 +434,7 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
   return VLB_OK;
 }
 
+
 // Lattice pass with list buffer `lists`; STEP and INIT also clear the other
 // list buffer for the next particle step.
 static vlb_status launch_lattice(vlb_handle* h, int mode, int src_buf, int dst_buf, int lists) {
@@ -461,6 +463,51 @@ static void advance_band_stamp(vlb_handle* h, long long levels) {
 }
 static void next_band_stamp(vlb_handle* h) { advance_band_stamp(h, 1); }
 
+// Particles [first, first + count) of the host vectors to the device: state,
+// properties and the per-particle constants of Eqs. 26, 29 (disk, rho_f = 1)
+// and the wall contact factor.  The update starts from rest of the inside
+// fluid terms (previous velocities = current ones).
+static vlb_status upload_particles(vlb_handle* h, int first, int count) {
+  const vlb_params& p = h->p;
+  std::vector<double> lam(count), pk((size_t)8 * count, 0.0);
+  const double lam_f = (p.tau_f - 0.5) / 3.0 / p.prandtl;
+  const double gmag = std::hypot(p.gravity[0], p.gravity[1]);
+  const double cscale = std::fabs(p.rho_ratio - 1.0) * gmag * M_PI;
+  for (int k = 0; k < count; ++k) {
+    lam[k] = h->hk[first + k] * lam_f;
+    const double R = h->hr[first + k], area = M_PI * R * R;
+    const double M = p.rho_ratio * area, I = 0.5 * M * R * R;
+    double* q = pk.data() + 8 * (size_t)k;
+    q[0] = 1.0 / M;
+    q[1] = 1.0 / I;
+    q[2] = area;                // M_in = rho_f M / rho_s
+    q[3] = 0.5 * area * R * R;  // I_in
+    q[4] = (p.rho_ratio - 1.0) * area;
+    q[5] = cscale * R * R / p.contact_eps_w;
+  }
+  const size_t b = count * sizeof(double);
+  auto up = [&](double* dst, const double* src) {
+    return cudaMemcpyAsync(dst + first, src, b, cudaMemcpyHostToDevice, h->stream);
+  };
+  CK(h, up(h->P.x, h->hx.data() + first));
+  CK(h, up(h->P.y, h->hy.data() + first));
+  CK(h, up(h->P.r, h->hr.data() + first));
+  CK(h, up(h->P.T0, h->hT0.data() + first));
+  CK(h, up(h->P.lam_s, lam.data()));
+  CK(h, cudaMemcpyAsync(h->P.fixed_T + first, h->hfix.data() + first, count * sizeof(int), cudaMemcpyHostToDevice,
+                        h->stream));
+  CK(h, up(h->P.ux, h->hux.data() + first));
+  CK(h, up(h->P.uy, h->huy.data() + first));
+  CK(h, up(h->P.om, h->hom.data() + first));
+  CK(h, up(h->P.ux_prev, h->hux.data() + first));
+  CK(h, up(h->P.uy_prev, h->huy.data() + first));
+  CK(h, up(h->P.om_prev, h->hom.data() + first));
+  CK(h, cudaMemcpyAsync(h->P.pk + 8 * (size_t)first, pk.data(), pk.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));  // the staging vectors end here
+  return VLB_OK;
+}
+
 static vlb_status initialize(vlb_handle* h) {
   const vlb_params& p = h->p;
   const int n = h->np;
@@ -470,45 +517,19 @@ static vlb_status initialize(vlb_handle* h) {
   double rmax = 0.0;
   for (double r : h->hr) rmax = std::max(rmax, r);
   const int band_off = band_offset(rmax);
-  if (n > 0) {
-    // exchange accumulators: zero before the first (initial) lattice pass
-    CK(h, cudaMalloc(&h->P.mes, (size_t)n * 6 * sizeof(unsigned long long)));
-    CK(h, cudaMemsetAsync(h->P.mes, 0, (size_t)n * 6 * sizeof(unsigned long long), h->stream));
+  if (h->cap > 0) {
+    // exchange accumulators and band tables for max_particles disks (later
+    // insertions append to them): zero before the first lattice pass
+    const size_t capn = (size_t)h->cap;
+    CK(h, cudaMalloc(&h->P.mes, capn * 6 * sizeof(unsigned long long)));
+    CK(h, cudaMemsetAsync(h->P.mes, 0, capn * 6 * sizeof(unsigned long long), h->stream));
     const size_t bw = 2 * (size_t)band_off + 1;
-    CK(h, cudaMalloc(&h->P.band, (size_t)n * bw * bw * sizeof(int2)));
-    CK(h, cudaMemsetAsync(h->P.band, 0, (size_t)n * bw * bw * sizeof(int2), h->stream));
-    std::vector<double> lam(n);
-    const double lam_f = (p.tau_f - 0.5) / 3.0 / p.prandtl;
-    for (int k = 0; k < n; ++k) lam[k] = h->hk[k] * lam_f;
-    const size_t b = n * sizeof(double);
-    CK(h, cudaMemcpyAsync(h->P.x, h->hx.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.y, h->hy.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.r, h->hr.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.T0, h->hT0.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.lam_s, lam.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.fixed_T, h->hfix.data(), n * sizeof(int), cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.ux, h->hux.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.uy, h->huy.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.om, h->hom.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.ux_prev, h->hux.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.uy_prev, h->huy.data(), b, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->P.om_prev, h->hom.data(), b, cudaMemcpyHostToDevice, h->stream));
-    // per-particle constants of Eqs. 26, 29 (disk, rho_f = 1) and the wall contact factor
-    std::vector<double> pk((size_t)8 * n, 0.0);
-    const double gmag = std::hypot(p.gravity[0], p.gravity[1]);
-    const double cscale = std::fabs(p.rho_ratio - 1.0) * gmag * M_PI;
-    for (int k = 0; k < n; ++k) {
-      const double R = h->hr[k], area = M_PI * R * R;
-      const double M = p.rho_ratio * area, I = 0.5 * M * R * R;
-      pk[8 * k + 0] = 1.0 / M;
-      pk[8 * k + 1] = 1.0 / I;
-      pk[8 * k + 2] = area;                 // M_in = rho_f M / rho_s
-      pk[8 * k + 3] = 0.5 * area * R * R;   // I_in
-      pk[8 * k + 4] = (p.rho_ratio - 1.0) * area;
-      pk[8 * k + 5] = cscale * R * R / p.contact_eps_w;
-    }
-    CK(h, cudaMemcpyAsync(h->P.pk, pk.data(), pk.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));  // host vectors may be reused below
+    CK(h, cudaMalloc(&h->P.band, capn * bw * bw * sizeof(int2)));
+    CK(h, cudaMemsetAsync(h->P.band, 0, capn * bw * bw * sizeof(int2), h->stream));
+  }
+  if (n > 0) {
+    vlb_status st = upload_particles(h, 0, n);
+    if (st != VLB_OK) return st;
   }
   fill_const(h, h->K32);
   fill_const(h, h->K64);
@@ -559,6 +580,65 @@ static vlb_status step_once(vlb_handle* h) {
   h->cur = 1 - h->cur;
   ++h->step;
   h->macros_valid = false;
+  return VLB_OK;
+}
+
+vlb_status vlb_insert_particles(vlb_handle* h, int32_t n, const double* xy, const double* radius, const double* T0,
+                                const double* k_ratio, const double* uv, const double* omega) {
+  if (!h) return VLB_EINVAL;
+  if (!h->initialized) return vlb_add_particles(h, n, xy, radius, T0, k_ratio, uv, omega);
+  if (n < 0 || (n > 0 && (!xy || !radius || !T0))) return fail(h, VLB_EINVAL, "bad particle arrays");
+  if (n == 0) return VLB_OK;
+  if (h->np + n > h->cap) return fail(h, VLB_EOVERFLOW, "max_particles exceeded");
+  const vlb_params& p = h->p;
+  const double rcap = double(h->PC.band_off - 2);  // the band tables hold disks up to this radius
+  for (int k = 0; k < n; ++k) {
+    const double X = xy[2 * k], Y = xy[2 * k + 1], R = radius[k];
+    if (!(R >= 1.0) || !std::isfinite(X) || !std::isfinite(Y)) return fail(h, VLB_EINVAL, "radius < 1 or bad centre");
+    if (R > rcap)
+      return fail(h, VLB_EINVAL, "radius larger than the largest disk present at the first step (band-table size)");
+    const bool inx = p.periodic[0] ? (X - R - 1.0 >= 0.0 && X + R + 1.0 <= p.nx) : (X - R >= 0.0 && X + R <= p.nx);
+    const bool iny = p.periodic[1] ? (Y - R - 1.0 >= 0.0 && Y + R + 1.0 <= p.ny) : (Y - R >= 0.0 && Y + R <= p.ny);
+    if (!inx || !iny) return fail(h, VLB_EINVAL, "particle outside the domain or across a periodic boundary");
+    if (k_ratio && !(k_ratio[k] > 0.0)) return fail(h, VLB_EINVAL, "k_ratio must be positive");
+  }
+  // overlap against the disks where they are now, and among the new ones
+  vlb_status st = vlb_synchronize(h);
+  if (st != VLB_OK) return st;
+  const int n0 = h->np;
+  std::vector<double> X(n0), Y(n0);
+  if (n0 > 0) {
+    CK(h, cudaMemcpy(X.data(), h->P.x, n0 * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(Y.data(), h->P.y, n0 * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  for (int k = 0; k < n; ++k) {
+    const double x = xy[2 * k], y = xy[2 * k + 1], r = radius[k];
+    for (int i = 0; i < n0; ++i) {
+      const double dx = x - X[i], dy = y - Y[i], rr = r + h->hr[i];
+      if (dx * dx + dy * dy < rr * rr) return fail(h, VLB_EINVAL, "particles overlap");
+    }
+    for (int j = 0; j < k; ++j) {
+      const double dx = x - xy[2 * j], dy = y - xy[2 * j + 1], rr = r + radius[j];
+      if (dx * dx + dy * dy < rr * rr) return fail(h, VLB_EINVAL, "particles overlap");
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    h->hx.push_back(xy[2 * k]);
+    h->hy.push_back(xy[2 * k + 1]);
+    h->hr.push_back(radius[k]);
+    h->hT0.push_back(T0[k]);
+    h->hk.push_back(k_ratio ? k_ratio[k] : p.k_ratio_default);
+    h->hfix.push_back(0);
+    h->hux.push_back(uv ? uv[2 * k] : 0.0);
+    h->huy.push_back(uv ? uv[2 * k + 1] : 0.0);
+    h->hom.push_back(omega ? omega[k] : 0.0);
+  }
+  // the entries beyond the old count are still as created: zero angle, force,
+  // partner count and exchange sums, band tables without a valid stamp
+  if ((st = upload_particles(h, n0, n)) != VLB_OK) return st;
+  h->np = n0 + n;
+  h->PC.np = h->np;
+  h->K32.np = h->K64.np = h->np;
   return VLB_OK;
 }
 

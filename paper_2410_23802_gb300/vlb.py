@@ -84,6 +84,7 @@ def _load():
         "vlb_set_fixed_temperature": (ctypes.c_int, [h, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
         "vlb_add_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
         "vlb_step": (ctypes.c_int, [h, ctypes.c_int32]),
+        "vlb_insert_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
         "vlb_step_batch": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
         "vlb_synchronize": (ctypes.c_int, [h]),
         "vlb_get_step": (ctypes.c_int, [h, P(ctypes.c_int64)]),
@@ -170,6 +171,17 @@ def vlb_add_particles(h, xy, radius, T0, k_ratio=None, uv=None, omega=None):
     conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)  # noqa: E731
     k_ratio, uv, omega = conv(k_ratio), conv(uv), conv(omega)
     _check(_lib.vlb_add_particles(h, n, _ptr(xy), _ptr(radius), _ptr(T0), _ptr(k_ratio), _ptr(uv), _ptr(omega)), h)
+
+
+def vlb_insert_particles(h, xy, radius, T0, k_ratio=None, uv=None, omega=None):
+    """Add disks between two steps (mid-run insertion)."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+    radius = np.ascontiguousarray(radius, dtype=np.float64)
+    T0 = np.ascontiguousarray(T0, dtype=np.float64)
+    conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)  # noqa: E731
+    k_ratio, uv, omega = conv(k_ratio), conv(uv), conv(omega)
+    _check(_lib.vlb_insert_particles(h, radius.shape[0], _ptr(xy), _ptr(radius), _ptr(T0), _ptr(k_ratio), _ptr(uv),
+                                     _ptr(omega)), h)
 
 
 def vlb_step(h, nsteps: int = 1):
@@ -347,6 +359,9 @@ class Lattice:
 
     def step(self, n: int = 1):
         vlb_step(self.h, n)
+
+    def insert_particles(self, *a, **k):
+        vlb_insert_particles(self.h, *a, **k)
 
     def fields(self, mask: int = VLB_FIELD_ALL) -> dict:
         return vlb_get_fields(self.h, self.nx, self.ny, mask)

@@ -67,3 +67,38 @@ def test_contact_third_law_and_wall_force():
                                         periodic=(True, True)), [(0, 1)])
         assert fij[0, 0] == -fij[1, 0] and fij[0, 1] == -fij[1, 1]
         assert fij[0, 0] * (X[i] - X[j]) > 0  # repulsive
+
+
+def test_insertion_into_a_rest_state_keeps_it_at_rest():
+    """Mid-run insertion (reading R12) pinned by what must not change: disks
+    of the fluid's density inserted at rest into a fluid at rest at one
+    temperature, without gravity, leave the flow at rest, the temperature
+    uniform and the mass of the closed box unchanged, whatever R_cv and
+    R_lambda (only f_s and c_v change)."""
+    import numpy as np
+    from oracle import vlbref as O
+    prm = O.Params(nx=48, ny=40, tau_f=0.8, rho_ratio=1.0, cv_ratio=2.5, k_ratio_default=4.0, T_fluid_init=0.6,
+                   T_ref=0.6)
+    sim = O.Simulation(prm, [14.0], [12.0], [5.0], [0.6])
+    sim.step(5)
+    m0 = sim.audit()[0]
+    sim.insert_particles([31.3, 20.2], [25.6, 30.1], [6.0, 4.5], [0.6, 0.6], k_ratio=[0.3, 8.0])
+    sim.step(20)
+    assert np.abs(sim.ux).max() < 1e-14 and np.abs(sim.uy).max() < 1e-14
+    assert np.abs(sim.T - 0.6).max() < 1e-13
+    assert abs(sim.audit()[0] / m0 - 1) < 1e-14
+    assert (sim.ras.fs > 0).sum() > 200  # the new disks are in the raster
+
+
+def test_insertion_before_the_first_step_equals_construction():
+    import numpy as np
+    from oracle import vlbref as O
+    prm = O.Params(nx=40, ny=40, rho_ratio=1.4, gravity=(0.0, -1e-4), beta=2.0, T_ref=1.0)
+    a = O.Simulation(prm, [12.0, 28.0], [26.0, 20.0], [5.0, 4.0], [0.0, 0.5])
+    st, h = O.vlbref_create(prm)
+    O.vlbref_add_particles(h, 1, [12.0, 26.0], [5.0], [0.0])
+    O.vlbref_insert_particles(h, 1, [28.0, 20.0], [4.0], [0.5])
+    O.vlbref_step(h, 6)
+    a.step(6)
+    assert np.array_equal(h.sim.fields()["T"], a.fields()["T"])
+    assert np.array_equal(h.sim.particle_state()["y"], a.particle_state()["y"])
