@@ -127,8 +127,8 @@ vlb_status vlb_params_default(vlb_params* p);
 vlb_status vlb_create(const vlb_params* p, vlb_handle** out);
 
 /* Hold particles [first, first + n) at their temperature T0 (held[k] != 0)
- * or let them conduct (held[k] == 0, the default): the paper's first
- * sedimentation case of Sec. 3.4 keeps the particle "at T_c".  Reading: in
+ * or let them conduct (held[k] == 0, the default): in the held-temperature
+ * sedimentation case of Sec. 3.3 the particle stays at T_c.  Reading: in
  * the part of a cell such a particle covers, the thermal populations are
  * replaced by the equilibrium at T0 in the volumetric form of Eq. 8,
  * g = (1 - f_fix) g + sum_p f_s,p g^eq(c_vs T0_p, T0_p).  Only before the
@@ -261,7 +261,9 @@ vlb_status vlb_get_solid_fraction(vlb_handle* h, uint8_t* count, int32_t* owner,
  *     contents (each call overwrites everything it reads back).
  *   - Calls that overlap on the GPU race on the array: serialise them.
  *   - The first call on a device looks the array up with
- *     cudaGetSymbolAddress; make it before any stream capture. */
+ *     cudaGetSymbolAddress; make it before any stream capture.
+ *   - The device that was current at vlb_create must be current at the call
+ *     (the array's address is per device): otherwise VLB_EINVAL. */
 #define VLB_NOALLOC_MAX_CELLS 65536
 vlb_status vlb_get_solid_fraction_noalloc(vlb_handle* h, uint8_t* count, int32_t* owner, uint8_t* flag,
                                           double* fsp);

@@ -12,10 +12,14 @@ Every function cites the equation or section of the paper it writes out.
 Readings of passages where the paper is silent are listed in the module
 docstring of :mod:`oracle.vlbref`.
 
-Parity status: every function is pinned by a ``-m "not gpu"`` test except the
-fully coupled many-step trajectory (flow + heat + particles), for which no
-closed form exists: "parity unpinned" beyond the invariants (mass, energy
-bookkeeping, isothermal invariant of Appendix A, u = u_s in solid cells,
-Galilean zero force) that the tests check on coupled runs.
+Parity status: every function is pinned by a ``-m "not gpu"`` test (the
+momentum-exchange force and torque by the linear and angular momentum
+balances of every step and by Stokes drag and torque; the buoyancy and the
+joint temperature/velocity solve by exact buoyant Poiseuille, conduction-slot
+and stratified-layer states), except the fully coupled many-step trajectory
+(flow + heat + particles), for which no closed form exists: "parity
+unpinned" beyond the invariants (mass, energy bookkeeping, isothermal
+invariant of Appendix A, u = u_s in solid cells, Galilean zero force, the
+momentum balances) that the tests check on coupled runs.
 """
 from .vlbref import *  # noqa: F401,F403

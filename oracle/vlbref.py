@@ -442,8 +442,8 @@ def geq(eps, T, cref):
 
 
 def fixed_temperature_correction(g, ras, T_p, fixed, cv_s, cref):
-    """Particles held at their own temperature (Sec. 3.4, first case: "the
-    temperatures of the solid particle ... are kept at T_c"; reading R11): in
+    """Particles held at their own temperature (Sec. 3.3, where the particle
+    stays at the cold temperature T_c throughout; reading R11): in
     the part of a cell that such a particle covers, the thermal populations
     are replaced by the equilibrium at the particle's temperature, in the
     volumetric form of Eq. 8:
@@ -932,6 +932,23 @@ VLBREF_OK, VLBREF_EINVAL, VLBREF_ESTATE = 0, -1, -4
 VLBREF_FIELD_RHO, VLBREF_FIELD_UX, VLBREF_FIELD_UY, VLBREF_FIELD_T, VLBREF_FIELD_FS = 1, 2, 4, 8, 16
 
 
+def _inside(prm, x, y, r):
+    """A disk lies inside the walls; on a periodic axis it keeps R + 1 from
+    the boundary (reading R7)."""
+    mx = r + 1.0 if prm.periodic[0] else r
+    my = r + 1.0 if prm.periodic[1] else r
+    return r > 0 and mx <= x <= prm.nx - mx and my <= y <= prm.ny - my
+
+
+def _min_image(d, L, periodic):
+    """Separation along an axis of length L; the nearest image on a
+    periodic axis."""
+    if not periodic:
+        return d
+    return np.where(d > 0.5 * L, d - L, np.where(d < -0.5 * L, d + L, d)) if isinstance(d, np.ndarray) else (
+        d - L if d > 0.5 * L else (d + L if d < -0.5 * L else d))
+
+
 class _RefHandle:
     def __init__(self, prm: Params):
         self.prm = prm
@@ -961,10 +978,11 @@ def vlbref_add_particles(h, n, xy, radius, T0, k_ratio=None, uv=None, omega=None
     P = h.parts
     for k in range(n):
         x, y, r = float(xy[2 * k]), float(xy[2 * k + 1]), float(radius[k])
-        if not (r > 0 and r <= x <= h.prm.nx - r and r <= y <= h.prm.ny - r):
-            return h.fail(VLBREF_EINVAL, "a disk lies outside the walls")
+        if not _inside(h.prm, x, y, r):
+            return h.fail(VLBREF_EINVAL, "a disk lies outside the walls or across a periodic boundary")
         for x2, y2, r2 in zip(P["x"], P["y"], P["r"]):
-            if (x - x2) ** 2 + (y - y2) ** 2 < (r + r2) ** 2:
+            dx, dy = _min_image(x - x2, h.prm.nx, h.prm.periodic[0]), _min_image(y - y2, h.prm.ny, h.prm.periodic[1])
+            if dx ** 2 + dy ** 2 < (r + r2) ** 2:
                 return h.fail(VLBREF_EINVAL, "particles overlap")
         P["x"].append(x)
         P["y"].append(y)
@@ -1005,10 +1023,17 @@ def vlbref_insert_particles(h, n, xy, radius, T0, k_ratio=None, uv=None, omega=N
     P = h.sim.part
     for k in range(n):
         x, y, r = float(xy[2 * k]), float(xy[2 * k + 1]), float(radius[k])
-        if not (r > 0 and r <= x <= h.prm.nx - r and r <= y <= h.prm.ny - r):
-            return h.fail(VLBREF_EINVAL, "a disk lies outside the walls")
-        if ((P["x"] - x) ** 2 + (P["y"] - y) ** 2 < (P["r"] + r) ** 2).any():
+        if not _inside(h.prm, x, y, r):
+            return h.fail(VLBREF_EINVAL, "a disk lies outside the walls or across a periodic boundary")
+        dx = _min_image(P["x"] - x, h.prm.nx, h.prm.periodic[0])
+        dy = _min_image(P["y"] - y, h.prm.ny, h.prm.periodic[1])
+        if (dx ** 2 + dy ** 2 < (P["r"] + r) ** 2).any():
             return h.fail(VLBREF_EINVAL, "particles overlap")
+        for j in range(k):
+            dx = _min_image(x - float(xy[2 * j]), h.prm.nx, h.prm.periodic[0])
+            dy = _min_image(y - float(xy[2 * j + 1]), h.prm.ny, h.prm.periodic[1])
+            if dx ** 2 + dy ** 2 < (r + float(radius[j])) ** 2:
+                return h.fail(VLBREF_EINVAL, "particles overlap")
     h.sim.insert_particles(xy[0:2 * n:2], xy[1:2 * n:2], list(radius[:n]), list(T0[:n]),
                            k_ratio=None if k_ratio is None else list(k_ratio[:n]),
                            ux=None if uv is None else uv[0:2 * n:2], uy=None if uv is None else uv[1:2 * n:2],

@@ -32,6 +32,7 @@ struct vlb_handle {
   std::string err;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  int device = 0;  // the device current at vlb_create, which holds every buffer
   int nx = 0, ny = 0, pitch = 0, ntx = 0, nty = 0;
   long long plane = 0;
   size_t ssize = 0;          // bytes per stored population
@@ -257,6 +258,14 @@ static Layout layout_of(const vlb_params& p) {
   return L;
 }
 static size_t a256(size_t b) { return (b + 255) / 256 * 256; }
+// Separation d of two centres along an axis of length L: on a periodic axis
+// the nearest image, so that disks meeting across the boundary count as close.
+static double min_image(double d, int L, int periodic) {
+  if (!periodic) return d;
+  if (d > 0.5 * L) return d - L;
+  if (d < -0.5 * L) return d + L;
+  return d;
+}
 // The particle block: 15 doubles, one int4, NBR_CAP + 2 ints, 8 doubles and
 // one raster record per particle, every sub-array on a 256-byte boundary.
 static size_t particle_block_bytes(size_t capn) {
@@ -322,6 +331,7 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
     return e == cudaErrorMemoryAllocation ? VLB_ENOMEM : VLB_ECUDA;
   };
   cudaError_t e;
+  if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(e, "device");
   if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e, "stream");
   h->own_stream = true;
   const size_t popbytes = (size_t)18 * h->plane * h->ssize;
@@ -403,7 +413,7 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
     if (!inx || !iny) return fail(h, VLB_EINVAL, "particle outside the domain or across a periodic boundary");
     if (k_ratio && !(k_ratio[k] > 0.0)) return fail(h, VLB_EINVAL, "k_ratio must be positive");
   }
-  // overlap test against existing and new disks
+  // overlap test against existing and new disks (minimum image on periodic axes)
   std::vector<double> X(h->hx), Y(h->hy), Rr(h->hr);
   for (int k = 0; k < n; ++k) { X.push_back(xy[2 * k]); Y.push_back(xy[2 * k + 1]); Rr.push_back(radius[k]); }
   std::vector<int> order(X.size());
@@ -411,14 +421,24 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
   std::sort(order.begin(), order.end(), [&](int a, int b) { return X[a] < X[b]; });
   double rmax = 0.0;
   for (double r : Rr) rmax = std::max(rmax, r);
+  const size_t nold = h->hx.size();
+  auto overlap = [&](int i, int j) {
+    if ((size_t)i < nold && (size_t)j < nold) return false;
+    const double dx = min_image(X[i] - X[j], p.nx, p.periodic[0]);
+    const double dy = min_image(Y[i] - Y[j], p.ny, p.periodic[1]);
+    return dx * dx + dy * dy < (Rr[i] + Rr[j]) * (Rr[i] + Rr[j]);
+  };
   for (size_t a = 0; a < order.size(); ++a)
     for (size_t b = a + 1; b < order.size(); ++b) {
       const int i = order[a], j = order[b];
       if (X[j] - X[i] > 2.0 * rmax) break;
-      if ((size_t)i < h->hx.size() && (size_t)j < h->hx.size()) continue;
-      const double dx = X[i] - X[j], dy = Y[i] - Y[j];
-      if (dx * dx + dy * dy < (Rr[i] + Rr[j]) * (Rr[i] + Rr[j])) return fail(h, VLB_EINVAL, "particles overlap");
+      if (overlap(i, j)) return fail(h, VLB_EINVAL, "particles overlap");
     }
+  if (p.periodic[0]) {  // pairs that meet across the periodic x boundary
+    for (size_t a = 0; a < order.size() && X[order[a]] < 2.0 * rmax; ++a)
+      for (size_t b = order.size(); b-- > a + 1 && X[order[b]] > p.nx - 2.0 * rmax;)
+        if (overlap(order[a], order[b])) return fail(h, VLB_EINVAL, "particles overlap");
+  }
   for (int k = 0; k < n; ++k) {
     h->hx.push_back(xy[2 * k]);
     h->hy.push_back(xy[2 * k + 1]);
@@ -614,11 +634,14 @@ vlb_status vlb_insert_particles(vlb_handle* h, int32_t n, const double* xy, cons
   for (int k = 0; k < n; ++k) {
     const double x = xy[2 * k], y = xy[2 * k + 1], r = radius[k];
     for (int i = 0; i < n0; ++i) {
-      const double dx = x - X[i], dy = y - Y[i], rr = r + h->hr[i];
+      const double dx = min_image(x - X[i], p.nx, p.periodic[0]), dy = min_image(y - Y[i], p.ny, p.periodic[1]);
+      const double rr = r + h->hr[i];
       if (dx * dx + dy * dy < rr * rr) return fail(h, VLB_EINVAL, "particles overlap");
     }
     for (int j = 0; j < k; ++j) {
-      const double dx = x - xy[2 * j], dy = y - xy[2 * j + 1], rr = r + radius[j];
+      const double dx = min_image(x - xy[2 * j], p.nx, p.periodic[0]);
+      const double dy = min_image(y - xy[2 * j + 1], p.ny, p.periodic[1]);
+      const double rr = r + radius[j];
       if (dx * dx + dy * dy < rr * rr) return fail(h, VLB_EINVAL, "particles overlap");
     }
   }
@@ -1248,6 +1271,8 @@ void vlb_destroy(vlb_handle* h) {
 // ---- helpers of the allocation-free entry point (vlb_noalloc.cu) ------------
 
 int64_t vlb_cells_of(const vlb_handle* h) { return (int64_t)h->nx * h->ny; }
+
+int vlb_device_of(const vlb_handle* h) { return h->device; }
 
 vlb_status vlb_fail_einval(vlb_handle* h, const char* msg) { return fail(h, VLB_EINVAL, msg); }
 

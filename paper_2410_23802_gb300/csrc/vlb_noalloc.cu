@@ -20,7 +20,10 @@
 //     caller;
 //   * the first call on each device looks up the array's device address with
 //     cudaGetSymbolAddress (with that device current); make that first call
-//     before any stream capture.
+//     before any stream capture;
+//   * the address is the one of the device that holds the handle, so the call
+//     requires that device to be current (VLB_EINVAL otherwise); after a
+//     cudaDeviceReset the library's handles and this address are both void.
 #include <cstdint>
 #include <mutex>
 
@@ -46,12 +49,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device (looked up once).
-cudaError_t scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of the scratch on device dev, which must be the current one
+// (looked up once per device).
+cudaError_t scratch_address(int dev, unsigned char** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaError_t e;
   std::lock_guard<std::mutex> lock(g_mutex);
   if (g_scratch_ptr[dev] == nullptr) {
     void* p = nullptr;
@@ -71,6 +73,7 @@ vlb_status vlb_solid_fraction_into(vlb_handle* h, unsigned char* d_count, int* d
                                    double* d_fsp, uint8_t* count, int32_t* owner, uint8_t* flag, double* fsp,
                                    bool require_initialized);
 int64_t vlb_cells_of(const vlb_handle* h);
+int vlb_device_of(const vlb_handle* h);
 vlb_status vlb_fail_einval(vlb_handle* h, const char* msg);
 vlb_status vlb_fail_cuda(vlb_handle* h, cudaError_t e, const char* where);
 
@@ -80,8 +83,14 @@ extern "C" vlb_status vlb_get_solid_fraction_noalloc(vlb_handle* h, uint8_t* cou
   if (vlb_cells_of(h) > (int64_t)kMaxCells)
     return vlb_fail_einval(h, "vlb_get_solid_fraction_noalloc: the lattice has more than "
                               "VLB_NOALLOC_MAX_CELLS (65536) cells");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return vlb_fail_cuda(h, e, "cudaGetDevice");
+  if (dev != vlb_device_of(h))
+    return vlb_fail_einval(h, "vlb_get_solid_fraction_noalloc: the current device is not the one that holds the "
+                              "handle (make it current first)");
   unsigned char* base = nullptr;
-  const cudaError_t e = scratch_address(&base);
+  e = scratch_address(dev, &base);
   if (e != cudaSuccess) return vlb_fail_cuda(h, e, "cudaGetSymbolAddress");
   double* d_fsp = reinterpret_cast<double*>(base);
   int* d_owner = reinterpret_cast<int*>(base + kFspBytes);

@@ -7,7 +7,7 @@ here.
 
 Cases
 -----
-channel   one cold disk settling in a closed channel (Sec. 3.4 proportions):
+channel   one cold disk settling in a closed channel (Secs. 3.3-3.4 proportions):
           100 x 400 cells, D = 20 at (50, 300), tau_f = 0.8, rho_s/rho_f = 1.5,
           g = 1e-5, fluid T = 1, particle T = 0, R_lambda = 2, R_cv = 1.5,
           Pr = 0.7, beta = 12.5 (Gr = 100 on D), adiabatic no-slip walls.
@@ -115,7 +115,7 @@ def channel(precision: str = "fp64") -> Case:
 
 def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision: str = "fp32") -> Case:
     """Sedimentation of a disk held at T_c = 0 in a long channel (the paper's
-    first Sec. 3.4 case, Table 4): D = 20 lu, width 4D, the disk starting D/2
+    Sec. 3.3 case, Table 4): D = 20 lu, width 4D, the disk starting D/2
     left of the centreline (x = 1.5 D), rho_r = 1.00232, Re = 40.5, Pr = 0.7,
     Grashof number gr, tau_f = 0.53, R_lambda = R_cv = 1; fluid and walls at
     T_h = 1 (T_ref = T_h).  The channel length is not given (length_d

@@ -38,6 +38,7 @@ def test_min_particle_temperature_matches_paper(r_cv):
     print(f"R_cv={r_cv}: min T inside {t_min:.4f}, paper {ref['min_T_inside'][str(r_cv)]}")
     assert abs(t_min - ref["min_T_inside"][str(r_cv)]) < 0.02
     # it settles downwards and stays on the centreline (FP32 rounding breaks the
-    # left-right symmetry only at the 1e-6 lu level over these steps)
+    # left-right symmetry only at the 1e-6 lu level over these steps: 1.3e-6
+    # measured; a real asymmetry of the method would move it much further)
     assert ps["uy"][0] < 0.0
-    assert abs(ps["x"][0] - 40.0) < 1e-3
+    assert abs(ps["x"][0] - 40.0) < 1e-5

@@ -1,5 +1,5 @@
-"""Particles held at their temperature (reading R11, the first sedimentation
-case of Sec. 3.4): the CUDA path against the FP64 oracle on a small cavity
+"""Particles held at their temperature (reading R11, the held-temperature
+sedimentation case of Sec. 3.3): the CUDA path against the FP64 oracle on a small cavity
 where some disks are held and the others conduct, in FP32 and FP64."""
 import dataclasses
 

@@ -62,3 +62,27 @@ def test_insertion_refusals():
         lat.insert_particles(NEW_XY[:1], NEW_R[:1], NEW_T[:1])
         lat.step(5)
         assert len(lat.particles()["x"]) == 9
+
+
+def test_no_disk_reaches_across_a_periodic_boundary():
+    """On a periodic axis a disk must keep R + 1 from the boundary (reading
+    R7), so two disks on opposite sides stay at least R1 + R2 + 2 apart
+    through it and can neither overlap nor touch there; a disk placed closer
+    to the boundary, which would touch one on the other side, is refused on
+    adding and on insertion, like the oracle's twin of the call."""
+    from oracle import vlbref as O
+    from paper_2410_23802_gb300 import vlb as V
+    params = dict(nx=96, ny=64, tau_f=0.8, prandtl=0.7, rho_ratio=1.5, cv_ratio=1.5, k_ratio_default=2.0,
+                  gravity=(0.0, -1e-5), beta=0.0, T_ref=1.0, T_fluid_init=1.0, periodic=(1, 0))
+    case = W.Case("periodic channel", params, [7.0], [30.0], [6.0], [0.0])
+    across = [[96.0 - 4.0, 30.0]]  # 9 lu from the first disk through the boundary, R1 + R2 = 11
+    with gpu_lattice(case, max_particles=3) as lat:
+        with pytest.raises(V.VlbError, match="EINVAL"):
+            lat.add_particles(across, [5.0], [0.0])
+        lat.add_particles([[90.0, 30.0]], [5.0], [0.0])  # R + 1 from the boundary, 13 lu through it: accepted
+        lat.step(3)
+        with pytest.raises(V.VlbError, match="EINVAL"):
+            lat.insert_particles(across, [5.0], [0.0])
+    st, h = O.vlbref_create(O.Params(**{**params, "periodic": (True, False)}))
+    assert O.vlbref_add_particles(h, 1, [7.0, 30.0], [6.0], [0.0]) == O.VLBREF_OK
+    assert O.vlbref_add_particles(h, 1, across[0], [5.0], [0.0]) == O.VLBREF_EINVAL
