@@ -11,6 +11,13 @@ sums.  Metric: coupled MLUPS (one lattice update = f and g at one cell).
 Under torchrun each rank runs its own replica of the case on its GPU (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
 
+On one GPU the same line also carries the other forms, each timed on its own
+(CUDA events, nvidia-smi clocks): `forms` (the same cavity with FP16 and BF16
+population storage), `batched` (256 channels stepped together with
+vlb_step_batch against the same cases one after the other) and `served` (a
+shortened seeded stream through the vlb_serve_* request loop against the
+plain path: cases/s, p50/p99 time to result).  --no-forms leaves them out.
+
 --workload channels: 256 independent single-disk channels (widths 64..256,
 4 widths long; workloads.channels), all resident, stepped together with
 vlb_step_batch (one launch of each kernel per step for all cases), against
@@ -161,9 +168,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _make_case(args):
+def _make_case(args, precision=None):
     from paper_2410_23802_gb300 import workloads as W
-    return W.cavity(side=args.side, n=args.particles, precision=args.precision)
+    return W.cavity(side=args.side, n=args.particles, precision=precision or args.precision)
 
 
 def _params(case, V):
@@ -171,6 +178,51 @@ def _params(case, V):
     prec = {"fp64": V.VLB_FP64, "fp32": V.VLB_FP32, "fp16": V.VLB_FP16_STORE,
             "bf16": V.VLB_BF16_STORE}[case.params["precision"]]
     return V.vlb_params_default(precision=prec, max_particles=len(case.x), **prm)
+
+
+def _time_cavity(case, V, stream, warmup, steps, local, world):
+    """K device-resident steps of one cavity case after W untimed ones, timed
+    with CUDA events on the library's stream (a torch stream passed through
+    vlb_set_stream), with the lattice kernel's own launches timed by the
+    library's profiling events and nvidia-smi sampled meanwhile."""
+    import numpy as np
+    import torch
+    lat = V.Lattice(_params(case, V))
+    V.vlb_set_stream(lat.h, stream.cuda_stream)
+    lat.add_particles(np.column_stack([case.x, case.y]), case.radius, case.T0, k_ratio=case.k_ratio)
+    with torch.cuda.stream(stream):
+        lat.step(warmup)
+        V.vlb_synchronize(lat.h)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        V.vlb_profile_begin(lat.h, steps)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        lat.step(steps)
+        t1.record(stream)
+        V.vlb_synchronize(lat.h)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    lattice_ms, lattice_launches, launches_per_step = V.vlb_profile_end(lat.h)
+    lat.close()
+    return elapsed_ms, lattice_ms, lattice_launches, launches_per_step, clocks
+
+
+def _roofline(precision, cells, lattice_ms, lattice_launches, key):
+    peak, peak_kind = _peaks()
+    lattice_avg_s = lattice_ms * 1e-3 / max(lattice_launches, 1)
+    bpc = BYTES_PER_CELL[precision]
+    achieved = bpc * cells / lattice_avg_s / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(key),
+            "kernel": "lattice_kernel<STEP>", "bytes_per_cell": bpc, "peak_kind": peak_kind,
+            "avg_launch_us": round(lattice_avg_s * 1e6, 2)}
 
 
 def run_ours(args):
@@ -190,33 +242,11 @@ def run_ours(args):
     xy = np.column_stack([case.x, case.y])
 
     # ---- device-resident throughput ------------------------------------------
-    lat = V.Lattice(_params(case, V))
-    V.vlb_set_stream(lat.h, stream.cuda_stream)
-    lat.add_particles(xy, case.radius, case.T0, k_ratio=case.k_ratio)
-    with torch.cuda.stream(stream):
-        lat.step(args.warmup)
-        V.vlb_synchronize(lat.h)
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        sampler = ClockSampler(local)
-        sampler.start()
-        time.sleep(0.3)
-        V.vlb_profile_begin(lat.h, args.steps)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        lat.step(args.steps)
-        t1.record(stream)
-        V.vlb_synchronize(lat.h)
-        torch.cuda.synchronize()
-        clocks = sampler.stop()
-    elapsed_ms = t0.elapsed_time(t1)
-    lattice_ms, lattice_launches, launches_per_step = V.vlb_profile_end(lat.h)
+    elapsed_ms, lattice_ms, lattice_launches, launches_per_step, clocks = _time_cavity(
+        case, V, stream, args.warmup, args.steps, local, world)
     elapsed_ms = _max_over_ranks(elapsed_ms)
     if world > 1:
         torch.distributed.barrier()
-    lat.close()
 
     # ---- end to end through the public API with host buffers -------------------
     e2e_steps = args.steps
@@ -245,14 +275,28 @@ def run_ours(args):
     h2d = len(case.x) * (2 * 8 + 3 * 8)                         # centres, radius, T0, k_ratio (once)
     d2h = cells * 5 * 8 + e2e_steps * len(case.x) * 12 * 8     # five fields once; 12 state arrays every step
 
+    # ---- the other graded forms (1 GPU only: rank 0 of a one-rank job) ---------
+    forms = batched = served = None
+    if world == 1 and not args.no_forms:
+        forms = {}
+        for prec in ("fp16", "bf16"):
+            c2 = _make_case(args, precision=prec)
+            ms, lms, ll, lps, ck = _time_cavity(c2, V, stream, args.warmup, args.steps, local, world)
+            forms[prec] = {"value": round(cells * args.steps / (ms * 1e-3) / 1e6, 1), "unit": UNIT,
+                           "ms_per_step": round(ms / args.steps, 5),
+                           "vs_fp32": round(elapsed_ms / ms, 4),
+                           "roofline": _roofline(prec, cells, lms, ll, f"cavity{args.side}_{args.particles}_{prec}"),
+                           "gpu_launches": lps * args.steps, "clocks": ck,
+                           "storage": f"populations as {prec.upper()} deviations from the rest equilibrium, "
+                                      "FP32 arithmetic, FP64 particles"}
+        batched = measure_batched(V, local, n_cases=256, steps=args.steps, warmup=args.warmup)
+        served = measure_served(V, local, n_cases=args.serve_cases, steps=args.serve_case_steps)
+
     if rank != 0:
         return
     value = _job_mlups(world, cells, args.steps, elapsed_ms * 1e-3)
-    peak, peak_kind = _peaks()
-    lattice_avg_s = lattice_ms * 1e-3 / max(lattice_launches, 1)
-    bpc = BYTES_PER_CELL[args.precision]
-    achieved = bpc * cells / lattice_avg_s / 1e9
     key = f"cavity{args.side}_{args.particles}_{args.precision}"
+    bpc = BYTES_PER_CELL[args.precision]
     line = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -270,10 +314,7 @@ def run_ours(args):
         "config": {"workload": case.name, "cells": cells, "particles": len(case.x),
                    "storage": args.precision, "parallelism": f"replicas x{world}",
                    "l2": _l2_note(cells * bpc)},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": _ncu_traffic(key),
-                     "kernel": "lattice_kernel<STEP>", "bytes_per_cell": bpc, "peak_kind": peak_kind,
-                     "avg_launch_us": round(lattice_avg_s * 1e6, 2)},
+        "roofline": _roofline(args.precision, cells, lattice_ms, lattice_launches, key),
         "e2e": {"value": round(_job_mlups(world, cells, e2e_steps, e2e_s), 1), "unit": UNIT,
                 "h2d_bytes_per_step": round(h2d / e2e_steps, 1), "d2h_bytes_per_step": round(d2h / e2e_steps, 1),
                 "note": "create + host particle upload + steps, each step's particle state to host "
@@ -281,9 +322,202 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if forms is not None:
+        line["forms"] = forms
+        line["batched"] = batched
+        line["served"] = served
     if not args.no_cpu_baseline and world == 1:  # the host cores are timed at N = 1 only
         line["cpu_baseline"] = cpu_baseline(args, budget_s=15.0)
     print(json.dumps(line), flush=True)
+
+
+def _channel_lattices(V, cases, streams):
+    import numpy as np
+    lats = []
+    for c, st in zip(cases, streams):
+        lat = V.Lattice(_params(c, V))
+        V.vlb_set_stream(lat.h, st.cuda_stream)
+        lat.add_particles(np.column_stack([c.x, c.y]), c.radius, c.T0, k_ratio=c.k_ratio)
+        lats.append(lat)
+    return lats
+
+
+def measure_batched(V, local, n_cases, steps, warmup, precision="fp32"):
+    """The 256-channel configuration resident at once: K steps of all cases
+    with vlb_step_batch (one launch of each kernel per step for every case),
+    against the plain path (each case stepped with vlb_step, one after the
+    other on one stream).  Device time from CUDA events on a stream joined
+    with every case's stream."""
+    import torch
+    from paper_2410_23802_gb300 import workloads as W
+    cases = W.channels(n=n_cases, precision=precision)
+    cells = sum(c.cells for c in cases)
+    main_stream = torch.cuda.Stream()
+    streams = [torch.cuda.Stream() for _ in cases]
+    lats = _channel_lattices(V, cases, streams)
+    hs = [l.h for l in lats]
+
+    def timed(run, sts):
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(main_stream)
+        for st in sts:
+            st.wait_event(t0)
+        run()
+        for st in sts:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            main_stream.wait_event(ev)
+        t1.record(main_stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
+
+    V.vlb_step_batch(hs, warmup)
+    for l in lats:
+        V.vlb_synchronize(l.h)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.2)
+    batched_ms = timed(lambda: V.vlb_step_batch(hs, steps), streams)
+    clocks = sampler.stop()
+    for l in lats:  # the plain path: one stream, one case after the other
+        V.vlb_set_stream(l.h, streams[0].cuda_stream)
+    plain_ms = timed(lambda: [l.step(steps) for l in lats], streams[:1])
+    for l in lats:
+        l.close()
+    mlups = lambda ms: cells * steps / (ms * 1e-3) / 1e6  # noqa: E731
+    return {"value": round(mlups(batched_ms), 1), "unit": UNIT, "ms_per_step": round(batched_ms / steps, 5),
+            "cases_per_s": round(len(cases) * steps / (batched_ms * 1e-3) / 5000.0, 2),
+            "cases_per_s_note": "cases of 5000 steps each",
+            "plain": {"value": round(mlups(plain_ms), 1), "unit": UNIT,
+                      "cases_per_s": round(len(cases) * steps / (plain_ms * 1e-3) / 5000.0, 2),
+                      "note": "one stream, one case after the other with vlb_step"},
+            "vs_plain": round(plain_ms / batched_ms, 3),
+            "workload": f"{len(cases)} channels W~U{{64..256}} x 4W, 1 disk each, {cells} cells, {precision}",
+            "steps": steps, "warmup": warmup, "gpu_launches": 2 * steps, "clocks": clocks}
+
+
+def _serve_stream(n_cases, steps):
+    from paper_2410_23802_gb300 import workloads as W
+    items = W.served_cases(n=n_cases, steps=steps)
+    import numpy as np
+    gaps = np.array([g for g, _, _ in items])
+    return gaps, [(c, n) for _, c, n in items]
+
+
+def _plain_alone(V, stream_ptr, c, n):
+    """The plain path: one case on its own, FP32 populations, created,
+    stepped, read back to host memory and freed."""
+    import dataclasses
+
+    import numpy as np
+    lat = V.Lattice(_params(dataclasses.replace(c, params=dict(c.params, precision="fp32")), V))
+    V.vlb_set_stream(lat.h, stream_ptr)
+    lat.add_particles(np.column_stack([c.x, c.y]), c.radius, c.T0, k_ratio=c.k_ratio)
+    lat.step(n)
+    f, p = lat.fields(), lat.particles()
+    lat.close()
+    return f, p
+
+
+def _plain_run(V, stream_ptr, gaps, cases, rate):
+    """Arrivals at `rate` (None: all at once) served one after the other by
+    the plain path; time to result per case and the makespan."""
+    import numpy as np
+    arrive = np.cumsum(gaps) / rate if rate else np.zeros(len(cases))
+    start = time.perf_counter()
+    lat_s = []
+    for (c, n), ta in zip(cases, arrive):
+        now = time.perf_counter() - start
+        if now < ta:
+            time.sleep(ta - now)
+        _plain_alone(V, stream_ptr, c, n)
+        lat_s.append(time.perf_counter() - start - ta)
+    return np.array(lat_s), time.perf_counter() - start - arrive[0]
+
+
+def _served_run(V, gaps, cases, rate, budget_gb, round_steps):
+    """The same arrivals through the server (vlb_serve_*)."""
+    import numpy as np
+    arrive = np.cumsum(gaps) / rate if rate else np.zeros(len(cases))
+    # the server's clock starts a little after `start`: times to result
+    # below count from the arrival and may be overstated by that much
+    start = time.perf_counter()
+    srv = V.Server(hbm_budget=int(budget_gb * 1e9), steps_per_round=round_steps)
+    pending, lat_s = {}, {}
+    k = 0
+    while len(lat_s) < len(cases):
+        now = time.perf_counter() - start
+        while k < len(cases) and arrive[k] <= now:
+            c, n = cases[k]
+            pending[k] = srv.submit(_params(c, V), np.column_stack([c.x, c.y]), c.radius, c.T0, n,
+                                    k_ratio=c.k_ratio)
+            k += 1
+        q, a, d = srv.poll()
+        for j, cid in (list(pending.items()) if d else []):
+            inf = srv.info(cid)
+            if inf["state"] in (V.VLB_CASE_DONE, V.VLB_CASE_FAILED):
+                srv.take(cid)
+                lat_s[j] = inf["t_done"] - arrive[j]
+                del pending[j]
+        if q == 0 and a == 0 and k < len(cases):
+            wait = arrive[k] - (time.perf_counter() - start)
+            if wait > 0:
+                time.sleep(wait)
+    srv.close()
+    return np.array([lat_s[j] for j in range(len(cases))]), time.perf_counter() - start - arrive[0]
+
+
+def _latency_summary(lat_s, span, n, work):
+    import numpy as np
+    return {"p50_ms": round(1e3 * float(np.percentile(lat_s, 50)), 2),
+            "p99_ms": round(1e3 * float(np.percentile(lat_s, 99)), 2),
+            "cases_per_s": round(n / span, 2), "mlups": round(work / span / 1e6, 1)}
+
+
+def measure_served(V, local, n_cases, steps, budget_gb=2.0, round_steps=100, loads=(None, 1.2)):
+    """A shortened seeded stream of the served configuration (cavities of
+    side 2^U[6,10], 1-512 disks, half FP16 storage) through the server and
+    through the plain path (one case after the other, FP32): all arriving at
+    once (saturation), and Poisson arrivals at 1.2 x the plain path's
+    measured service rate.  Time to result = arrival to fields and particle
+    state in host memory."""
+    import torch
+    stream = torch.cuda.Stream()
+    gaps, cases = _serve_stream(n_cases, steps)
+    work = sum(c.cells * n for c, n in cases)
+    for c, n in cases[:3]:
+        _plain_alone(V, stream.cuda_stream, c, 20)
+    res = {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    lp, span_p = _plain_run(V, stream.cuda_stream, gaps, cases, None)
+    rate_plain = len(cases) / span_p
+    res["all_at_once"] = {"plain": _latency_summary(lp, span_p, len(cases), work)}
+    ls, span = _served_run(V, gaps, cases, None, budget_gb, round_steps)
+    res["all_at_once"]["served"] = _latency_summary(ls, span, len(cases), work)
+    for load in loads:
+        if load is None:
+            continue
+        rate = load * rate_plain
+        ls, span = _served_run(V, gaps, cases, rate, budget_gb, round_steps)
+        lp, span_p = _plain_run(V, stream.cuda_stream, gaps, cases, rate)
+        res[f"poisson_{load}x"] = {"offered_cases_per_s": round(rate, 2),
+                                   "served": _latency_summary(ls, span, len(cases), work),
+                                   "plain": _latency_summary(lp, span_p, len(cases), work)}
+    clocks = sampler.stop()
+    sat = res["all_at_once"]
+    return {"value": sat["served"]["mlups"], "unit": UNIT,
+            "cases_per_s": sat["served"]["cases_per_s"],
+            "vs_plain_cases_per_s": round(sat["served"]["cases_per_s"] / sat["plain"]["cases_per_s"], 3),
+            "workload": f"{len(cases)} seeded cavity cases, side 2^U[6,10], 1-512 disks of D~U[8,24], "
+                        f"half FP16 storage, {steps} steps each; HBM budget {budget_gb} GB, "
+                        f"{round_steps} steps per round",
+            "plain_service_rate": round(rate_plain, 2), "loads": res, "clocks": clocks,
+            "note": "value and cases_per_s: the server with every case arriving at once (saturation); "
+                    "plain: one case after the other with FP32 populations; wall clock from arrival to "
+                    "results in host memory"}
 
 
 def run_channels(args):
@@ -303,12 +537,7 @@ def run_channels(args):
     cells = sum(c.cells for c in cases)
     main_stream = torch.cuda.Stream()
     streams = [torch.cuda.Stream() for _ in cases]
-    lats = []
-    for c, st in zip(cases, streams):
-        lat = V.Lattice(_params(c, V))
-        V.vlb_set_stream(lat.h, st.cuda_stream)
-        lat.add_particles(list(zip(c.x, c.y)), c.radius, c.T0, k_ratio=c.k_ratio)
-        lats.append(lat)
+    lats = _channel_lattices(V, cases, streams)
     hs = [l.h for l in lats]
 
     def timed(run):
@@ -382,120 +611,22 @@ def run_channels(args):
 def run_serve(args):
     """Served mode (FP32 and FP16 storage, half each) against the plain
     path (one case after the other, FP32) under the same seeded arrivals:
-    Poisson arrivals at 0.8 and 1.2 times the plain path's measured service
-    rate, time to result (arrival to fields and particle state in host
-    memory) per case, aggregate MLUPS and cases/s over the makespan."""
-    import dataclasses
-
-    import numpy as np
+    all at once, and Poisson arrivals at 0.8 and 1.2 times the plain path's
+    measured service rate; time to result (arrival to fields and particle
+    state in host memory) per case, aggregate MLUPS and cases/s over the
+    makespan."""
     import torch
     from paper_2410_23802_gb300 import vlb as V
-    from paper_2410_23802_gb300 import workloads as W
 
     rank, world, local = _dist()
     if rank != 0:
         return
     torch.cuda.set_device(local)
-    stream = torch.cuda.Stream()
-    stream_ptr = stream.cuda_stream
-    items = W.served_cases(n=args.cases, steps=args.serve_steps)
-    gaps = np.array([g for g, _, _ in items])
-    cases = [(c, n) for _, c, n in items]
-    work = sum(c.cells * n for c, n in cases)
-
-    def params(c):
-        return _params(c, V)
-
-    def run_alone(c, n):
-        """The plain path: one case on its own, FP32 populations."""
-        lat = V.Lattice(_params(dataclasses.replace(c, params=dict(c.params, precision="fp32")), V))
-        V.vlb_set_stream(lat.h, stream_ptr)
-        lat.add_particles(np.column_stack([c.x, c.y]), c.radius, c.T0, k_ratio=c.k_ratio)
-        lat.step(n)
-        f, p = lat.fields(), lat.particles()
-        lat.close()
-        return f, p
-
-    # warm-up, then the plain service rate on a sample of the stream
-    for c, n in cases[:3]:
-        run_alone(c, 50)
-    sample = cases[: min(40, len(cases))]
-    t0 = time.perf_counter()
-    for c, n in sample:
-        run_alone(c, n)
-    rate_plain = len(sample) / (time.perf_counter() - t0)
-
-    def plain_run(rate):
-        arrive = np.cumsum(gaps) / rate
-        start = time.perf_counter()
-        lat_s = []
-        for (c, n), ta in zip(cases, arrive):
-            now = time.perf_counter() - start
-            if now < ta:
-                time.sleep(ta - now)
-            run_alone(c, n)
-            lat_s.append(time.perf_counter() - start - ta)
-        span = time.perf_counter() - start - arrive[0]
-        return np.array(lat_s), span
-
-    def served_run(rate):
-        arrive = np.cumsum(gaps) / rate if rate else np.zeros(len(cases))  # None: all at once
-        # the server's clock starts a little after `start`: times to result
-        # below count from the arrival and may be overstated by that much
-        start = time.perf_counter()
-        srv = V.Server(hbm_budget=int(args.budget_gb * 1e9), steps_per_round=args.round_steps)
-        pending, lat_s = {}, {}
-        k = 0
-        while len(lat_s) < len(cases):
-            now = time.perf_counter() - start
-            while k < len(cases) and arrive[k] <= now:
-                c, n = cases[k]
-                pending[k] = srv.submit(params(c), np.column_stack([c.x, c.y]), c.radius, c.T0, n,
-                                        k_ratio=c.k_ratio)
-                k += 1
-            q, a, d = srv.poll()
-            for j, cid in (list(pending.items()) if d else []):
-                inf = srv.info(cid)
-                if inf["state"] in (V.VLB_CASE_DONE, V.VLB_CASE_FAILED):
-                    srv.take(cid)
-                    lat_s[j] = inf["t_done"] - arrive[j]
-                    del pending[j]
-            if q == 0 and a == 0 and k < len(cases):
-                wait = arrive[k] - (time.perf_counter() - start)
-                if wait > 0:
-                    time.sleep(wait)
-        srv.close()
-        span = time.perf_counter() - start - arrive[0]
-        return np.array([lat_s[j] for j in range(len(cases))]), span
-
-    res = {}
-    clocks = None
-    for load in (0.8, 1.2):
-        rate = load * rate_plain
-        sampler = ClockSampler(local)
-        sampler.start()
-        ls, span = served_run(rate)
-        ck = sampler.stop()
-        clocks = clocks or ck
-        lp, span_p = plain_run(rate)
-        res[str(load)] = {
-            "offered_cases_per_s": round(rate, 2),
-            "served": {"p50_ms": round(1e3 * float(np.percentile(ls, 50)), 2),
-                       "p99_ms": round(1e3 * float(np.percentile(ls, 99)), 2),
-                       "cases_per_s": round(len(cases) / span, 2), "mlups": round(work / span / 1e6, 1)},
-            "plain": {"p50_ms": round(1e3 * float(np.percentile(lp, 50)), 2),
-                      "p99_ms": round(1e3 * float(np.percentile(lp, 99)), 2),
-                      "cases_per_s": round(len(cases) / span_p, 2), "mlups": round(work / span_p / 1e6, 1)},
-        }
-    ls, span = served_run(None)
-    res["all_at_once"] = {"served": {"p50_ms": round(1e3 * float(np.percentile(ls, 50)), 2),
-                                     "p99_ms": round(1e3 * float(np.percentile(ls, 99)), 2),
-                                     "cases_per_s": round(len(cases) / span, 2),
-                                     "mlups": round(work / span / 1e6, 1)}}
-    hi = res["1.2"]["served"]
+    r = measure_served(V, local, args.cases, args.serve_steps, budget_gb=args.budget_gb,
+                       round_steps=args.round_steps, loads=(None, 0.8, 1.2))
     line = {
         "metric": "served p50/p99 time to result (ms) and aggregate MLUPS",
-        "value": hi["mlups"],
+        "value": r["value"],
         "unit": "MLUPS",
         "n_gpus": 1,
         "steps": args.serve_steps,
@@ -505,15 +636,8 @@ def run_serve(args):
         "vs_baseline": None,
         "dtype": "f32 / f16 storage (half each)",
         "data": "synthetic (seeded SplitMix64 arrivals, sizes and placements)",
-        "config": {"workload": f"{len(cases)} cavity cases, side 2^U[6,10], 1-512 disks of D~U[8,24], "
-                               f"{args.serve_steps} steps each, Poisson arrivals",
-                   "hbm_budget_gb": args.budget_gb, "steps_per_round": args.round_steps},
-        "plain_service_rate": round(rate_plain, 2),
-        "loads": res,
-        "clocks": clocks,
-        "note": "value: aggregate MLUPS of the served run at 1.2x the plain service rate; "
-                "time to result = arrival to fields and particle state in host memory; "
-                "plain: one case after the other with FP32 populations",
+        "config": {"workload": r["workload"]},
+        **{k: v for k, v in r.items() if k not in ("value", "unit", "workload")},
     }
     print(json.dumps(line), flush=True)
 
@@ -662,6 +786,9 @@ def main():
     ap.add_argument("--serve-steps", type=int, default=2000)
     ap.add_argument("--budget-gb", type=float, default=2.0)
     ap.add_argument("--round-steps", type=int, default=100)
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16, batched and served sub-records")
+    ap.add_argument("--serve-cases", type=int, default=48, help="served sub-record: cases in the stream")
+    ap.add_argument("--serve-case-steps", type=int, default=400, help="served sub-record: steps per case")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -182,6 +182,11 @@ static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
   K.se_f = C(p.thermal_rates_mode == 0 ? 1.0 / (0.5 + 0.25 / (tgf - 0.5)) : 1.0);
   K.k3_cref = C(3.0 / cref);
   K.gk_f = C(-3.0 / (cref * tgf));
+  // L2 prefetch distance: whole occupancy waves of the step kernel
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) sms = 0;
+  const int per_sm = lattice_step_ctas_per_sm(p.precision == VLB_FP64, h->storage);
+  K.pf_tiles = sms * per_sm * lattice_prefetch_waves();
 }
 
 extern "C" {
