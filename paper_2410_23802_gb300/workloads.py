@@ -154,10 +154,10 @@ def conjugate_sedimentation(r_cv: float, length_d: float = 40.0, precision: str 
 
 
 def cavity(side: int = 2048, n: int = 2048, diameter: float = 16.0, seed: int = 20241031,
-           precision: str = "fp32", k_log_uniform: bool = False) -> Case:
+           precision: str = "fp32", k_log_uniform: bool = False, gap: float = 2.0) -> Case:
     nu = (0.8 - 0.5) / 3.0
     g = 1e-5
-    xs, ys = place_disks(side, side, n, diameter, seed)
+    xs, ys = place_disks(side, side, n, diameter, seed, gap=gap)
     params = dict(nx=side, ny=side, tau_f=0.8, prandtl=0.71, rho_ratio=1.2, cv_ratio=2.0, k_ratio_default=5.0,
                   gravity=(0.0, -g), beta=gr_beta(100.0, nu, g, 1.0, diameter), T_ref=1.0, T_fluid_init=1.0,
                   thermal_wall=(0, 0, 1, 1), wall_T=(0.0, 0.0, 1.0, 0.0), thermal_rates_mode=1,
