@@ -45,6 +45,21 @@ R6  Initial state: f* = f^eq(1, 0) corrected with f_s^0 (Eq. 8); the internal
     [df_s/dt]^0 = 0.
 R7  Domain: fractions exist only for cells inside the domain; a particle may
     not cross a periodic boundary.
+R13 Elliptical particles (Sec. 3.2 gives the shape, a = 2b, and its
+    orientation, nothing of how it is rasterised or touches others): the
+    exact area of ellipse ∩ cell, found in the ellipse's unit-disk frame
+    where the cell is a parallelogram; a cell is SOLID when its four corners
+    lie in the closed ellipse and FLUID when the ellipse's quadratic form
+    stays >= 1 over the cell, both decided in FP64; the orientation theta
+    advances as theta + Omega (forward Euler) and sets the raster; mass
+    rho_s pi a b, moment of inertia M (a^2 + b^2) / 4; contact between
+    particles through the circumscribed disks, with a wall through the
+    extent of the ellipse along the wall's normal.
+R14 Fully developed outflow (Sec. 3.2, the lower end of the long channel:
+    the normal derivative of u vanishes): a population entering through an
+    open side takes the value the same population has one cell further in
+    (zero normal gradient after streaming), for f and g alike; no wall
+    contact there.
 R12 Mid-run insertion (the paper has none): a disk added at level n joins the
     particle set and first appears in the raster of level n+1; the correction
     (Eq. 8) and the df_s/dt recursion (Eq. 24) then act on it as on a disk
@@ -213,21 +228,46 @@ def _source_index(nx, ny, i, periodic):
     return yy, xx, np.clip(sy, 0, ny - 1), np.clip(sx, 0, nx - 1), out_x, out_y, sy < 0, sx < 0
 
 
-def stream_flow(fbar, periodic=(False, False)):
+def _outflow_copy(dist, i, yy, xx, ox, oy, ylow, xlow, outflow):
+    """Zero normal gradient at open sides (reading R14, the fully developed
+    condition of Sec. 3.2): a population that would come from outside through
+    an open side takes the value the same population has one cell further in,
+    f*_i(x) = f*_i(x + n) = dist_i(x - e_i + n) with n the side's inward
+    normal.  Returns the mask of cells this applies to and the values.  A
+    population crossing a corner takes the rule of the x side when the y
+    side is open."""
+    ny, nx = yy.shape
+    side_x = np.where(xlow, 0, 1)
+    side_y = np.where(ylow, 2, 3)
+    open_x = np.asarray(outflow, dtype=bool)[side_x] & ox
+    open_y = np.asarray(outflow, dtype=bool)[side_y] & oy
+    # source one cell in from the crossed side(s): drop the crossing component of -e_i
+    sx = np.where(ox, xx, (xx - E[i, 0]) % nx)
+    sy = np.where(oy, yy, (yy - E[i, 1]) % ny)
+    mask = (open_y & ~ox) | (open_x & ~oy) | (open_x & open_y)
+    return mask, dist[i, sy, sx]
+
+
+def stream_flow(fbar, periodic=(False, False), outflow=(False, False, False, False)):
     """Linear streaming f*_i(x + e_i) = fbar_i(x) (Eq. 3b), written as a
     pull.  Where x - e_i lies outside the domain the population bounces back
-    halfway at the wall face: f*_i(x) = fbar_opp(i)(x)."""
+    halfway at the wall face: f*_i(x) = fbar_opp(i)(x); through an open
+    side (outflow) it takes the zero-gradient value (reading R14)."""
     _, ny, nx = fbar.shape
     out = np.empty_like(fbar)
     for i in range(9):
-        yy, xx, sy, sx, ox, oy, _, _ = _source_index(nx, ny, i, tuple(periodic))
+        yy, xx, sy, sx, ox, oy, ylow, xlow = _source_index(nx, ny, i, tuple(periodic))
         outside = ox | oy
         pulled = fbar[i, sy, sx]
-        out[i] = np.where(outside, fbar[OPP[i], yy, xx], pulled)
+        res = np.where(outside, fbar[OPP[i], yy, xx], pulled)
+        if any(outflow):
+            mask, copied = _outflow_copy(fbar, i, yy, xx, ox, oy, ylow, xlow, outflow)
+            res = np.where(mask, copied, res)
+        out[i] = res
     return out
 
 
-def stream_thermal(gbar, cref, thermal_wall, wall_T, periodic=(False, False)):
+def stream_thermal(gbar, cref, thermal_wall, wall_T, periodic=(False, False), outflow=(False, False, False, False)):
     """Streaming of g (Eq. 17b) as a pull.  At a wall (order x-, x+, y-, y+):
     adiabatic -> g_i(x) = gbar_opp(i)(x); held at T_w ->
     g_i(x) = -gbar_opp(i)(x) + 2 g_i^eq(T_w).  The moving components of
@@ -249,6 +289,19 @@ def stream_thermal(gbar, cref, thermal_wall, wall_T, periodic=(False, False)):
                 geq_w = geq_wall[w][i]
                 sel = (ox | oy) & (wall == w)
                 res = np.where(sel, -bounce + 2.0 * geq_w, res)
+        if any(outflow):
+            # open sides: zero normal gradient of g as of f (reading R14); a
+            # corner under an open y side takes the x side's rule
+            mask, copied = _outflow_copy(gbar, i, yy, xx, ox, oy, ylow, xlow, outflow)
+            res = np.where(mask, copied, res)
+            corner = ox & oy & np.asarray(outflow, dtype=bool)[np.where(ylow, 2, 3)] & \
+                ~np.asarray(outflow, dtype=bool)[np.where(xlow, 0, 1)]
+            xw = np.where(xlow, 0, 1)
+            cres = bounce.copy()
+            for w in (0, 1):
+                if thermal_wall[w] == 1:
+                    cres = np.where(xw == w, -bounce + 2.0 * geq_wall[w][i], cres)
+            res = np.where(corner, cres, res)
         out[i] = res
     return out
 
@@ -363,6 +416,152 @@ def rasterise(nx, ny, X, Y, R) -> Raster:
         flag[cj, ci, k] = cf
         fsp[cj, ci, k] = val
         count[cj, ci] = k + 1
+    tot = fsp.sum(axis=2)
+    scale = np.where(tot > 1.0, 1.0 / np.where(tot > 1.0, tot, 1.0), 1.0)
+    fsp = fsp * scale[:, :, None]
+    return Raster(fs=fsp.sum(axis=2), count=count, owner=owner, flag=flag, fsp=fsp)
+
+
+# --------------------------------------------------------------------------
+# Elliptical particles (Sec. 3.2; reading R13).
+# --------------------------------------------------------------------------
+
+
+def ellipse_frame(px, py, X, Y, a, b, c, s):
+    """Coordinates of the points (px, py) in the frame of the ellipse centred
+    at (X, Y) with semi-axes a (along its major axis, at angle theta to the
+    x axis, c = cos theta, s = sin theta) and b, scaled so that the ellipse is
+    the unit disk: (u / a, v / b), u = c dx + s dy, v = -s dx + c dy."""
+    dx = px - X
+    dy = py - Y
+    return (c * dx + s * dy) / a, (c * dy - s * dx) / b
+
+
+def ellipse_cell_class(i, j, X, Y, a, b, c, s):
+    """Class of cell [i, i+1] x [j, j+1] against the closed ellipse
+    (reading R13): SOLID when its four corners lie in the ellipse (then the
+    convex cell does), FLUID when the smallest value over the cell of
+    Q = (u/a)^2 + (v/b)^2 is >= 1 (the cell meets the ellipse at most in one
+    point), INTERFACE otherwise.  On each edge P0 + t d, t in [0, 1], Q is a
+    convex quadratic in t whose minimum sits at its vertex clamped to
+    [0, 1]."""
+    corners = [(i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)]
+    qc = []
+    for (xa, ya) in corners:
+        u, v = ellipse_frame(float(xa), float(ya), X, Y, a, b, c, s)
+        qc.append(u * u + v * v)
+    if max(qc) <= 1.0:
+        return SOLID
+    if i <= X <= i + 1 and j <= Y <= j + 1:
+        return INTERFACE  # the centre lies in the cell
+    qmin = min(qc)
+    for k in range(4):
+        x0, y0 = corners[k]
+        x1, y1 = corners[(k + 1) % 4]
+        u0, v0 = ellipse_frame(float(x0), float(y0), X, Y, a, b, c, s)
+        u1, v1 = ellipse_frame(float(x1), float(y1), X, Y, a, b, c, s)
+        du, dv = u1 - u0, v1 - v0
+        A = du * du + dv * dv
+        t = min(max(-(u0 * du + v0 * dv) / A, 0.0), 1.0)
+        uu, vv = u0 + t * du, v0 + t * dv
+        qmin = min(qmin, uu * uu + vv * vv)
+    return FLUID if qmin >= 1.0 else INTERFACE
+
+
+def polygon_unit_disk_area(us, vs):
+    """Area of the unit disk intersected with the convex polygon of vertices
+    (us[k], vs[k]) in counter-clockwise order, by Green's theorem on the
+    boundary of the intersection: the parts of the polygon's edges inside
+    the disk contribute (u dv - v du) / 2 = (u_a v_b - u_b v_a) / 2 each, and
+    the arcs of the circle between leaving the disk on one edge and entering
+    it on a later one contribute half their angle (counter-clockwise)."""
+    n = len(us)
+    pieces = []  # inside parts of the edges, in boundary order: (start, end)
+    for k in range(n):
+        u0, v0 = us[k], vs[k]
+        u1, v1 = us[(k + 1) % n], vs[(k + 1) % n]
+        du, dv = u1 - u0, v1 - v0
+        A = du * du + dv * dv
+        B = u0 * du + v0 * dv
+        C = u0 * u0 + v0 * v0 - 1.0
+        disc = B * B - A * C
+        if A == 0.0 or disc <= 0.0:
+            continue
+        r = math.sqrt(disc)
+        t0, t1 = max((-B - r) / A, 0.0), min((-B + r) / A, 1.0)
+        if t1 <= t0:
+            continue
+        pieces.append(((u0 + t0 * du, v0 + t0 * dv), (u0 + t1 * du, v0 + t1 * dv), k))
+    if not pieces:
+        # no edge meets the disk: the disk lies inside the polygon or outside it
+        inside = all((us[(k + 1) % n] - us[k]) * (0.0 - vs[k]) - (vs[(k + 1) % n] - vs[k]) * (0.0 - us[k]) >= 0.0
+                     for k in range(n))
+        return math.pi if inside else 0.0
+    area = 0.0
+    for m, (pa, pb, k) in enumerate(pieces):
+        area += 0.5 * (pa[0] * pb[1] - pb[0] * pa[1])
+        qa, _, k2 = pieces[(m + 1) % len(pieces)]  # where the boundary re-enters
+        if k2 == (k + 1) % n and math.hypot(qa[0] - pb[0], qa[1] - pb[1]) < 1e-12:
+            continue  # the boundary turns at a vertex on the circle: no arc (rounding put it either side)
+        ang = math.atan2(pb[0] * qa[1] - pb[1] * qa[0], pb[0] * qa[0] + pb[1] * qa[1])
+        if ang < 0.0:
+            ang += 2.0 * math.pi
+        area += 0.5 * ang
+    return area
+
+
+def ellipse_cell_area(i, j, X, Y, a, b, c, s):
+    """Exact area of the ellipse within cell [i, i+1] x [j, j+1]: the map to
+    the ellipse's unit-disk frame takes the cell to a parallelogram (same
+    orientation, area scaled by 1 / (a b))."""
+    corners = [(i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)]
+    us, vs = [], []
+    for (xa, ya) in corners:
+        u, v = ellipse_frame(float(xa), float(ya), X, Y, a, b, c, s)
+        us.append(u)
+        vs.append(v)
+    return a * b * polygon_unit_disk_area(us, vs)
+
+
+def rasterise_shapes(nx, ny, X, Y, A, B, theta) -> Raster:
+    """Solid-fraction field of a set of particles of which those with
+    A[p] != B[p] are ellipses (semi-axes A >= B, major axis at angle
+    theta[p]) and the others disks of radius A[p] (their cells exactly as
+    `rasterise` gives them).  Owners in ascending particle order, at most 4,
+    fractions scaled to sum 1 where they pass it."""
+    X, Y = np.asarray(X, dtype=np.float64), np.asarray(Y, dtype=np.float64)
+    A, B = np.asarray(A, dtype=np.float64), np.asarray(B, dtype=np.float64)
+    theta = np.asarray(theta, dtype=np.float64)
+    count = np.zeros((ny, nx), dtype=np.int64)
+    owner = np.full((ny, nx, MAX_OWNERS), -1, dtype=np.int64)
+    flag = np.zeros((ny, nx, MAX_OWNERS), dtype=np.int64)
+    fsp = np.zeros((ny, nx, MAX_OWNERS), dtype=np.float64)
+    for p in range(X.shape[0]):
+        if A[p] == B[p]:
+            one = rasterise(nx, ny, X[p:p + 1], Y[p:p + 1], A[p:p + 1])
+            jj, ii = np.nonzero(one.count)
+            cells = [(int(i), int(j), int(one.flag[j, i, 0]), float(one.fsp[j, i, 0])) for j, i in zip(jj, ii)]
+        else:
+            c, s = math.cos(theta[p]), math.sin(theta[p])
+            i0, i1 = max(int(math.floor(X[p] - A[p])) - 1, 0), min(int(math.ceil(X[p] + A[p])) + 1, nx - 1)
+            j0, j1 = max(int(math.floor(Y[p] - A[p])) - 1, 0), min(int(math.ceil(Y[p] + A[p])) + 1, ny - 1)
+            cells = []
+            for j in range(j0, j1 + 1):
+                for i in range(i0, i1 + 1):
+                    cls = ellipse_cell_class(i, j, X[p], Y[p], A[p], B[p], c, s)
+                    if cls == FLUID:
+                        continue
+                    val = 1.0 if cls == SOLID else min(max(ellipse_cell_area(i, j, X[p], Y[p], A[p], B[p], c, s),
+                                                           0.0), 1.0)
+                    cells.append((i, j, cls, val))
+        for i, j, cls, val in cells:
+            k = count[j, i]
+            if k >= MAX_OWNERS:
+                raise OverflowError("more than 4 particles own one cell")
+            owner[j, i, k] = p
+            flag[j, i, k] = cls
+            fsp[j, i, k] = val
+            count[j, i] = k + 1
     tot = fsp.sum(axis=2)
     scale = np.where(tot > 1.0, 1.0 / np.where(tot > 1.0, tot, 1.0), 1.0)
     fsp = fsp * scale[:, :, None]
@@ -559,9 +758,13 @@ def contact_pairs(X, Y, R, zeta):
     return pairs
 
 
-def contact_forces(X, Y, R, prm, pairs):
+def contact_forces(X, Y, R, prm, pairs, semi_minor=None, theta=None):
     """Contact force on each particle (reading R5); partners are summed in
-    ascending id, then walls x-, x+, y-, y+."""
+    ascending id, then walls x-, x+, y-, y+.  An ellipse (semi_minor < R, the
+    semi-major axis; major axis at angle theta) meets another particle as its
+    circumscribed disk and a wall by its extent along the wall's normal,
+    sqrt(a^2 cos^2 + b^2 sin^2) of the angle between major axis and normal
+    (reading R13)."""
     n = len(X)
     zeta = prm.contact_range
     gmag = math.hypot(prm.gravity[0], prm.gravity[1])
@@ -586,11 +789,18 @@ def contact_forces(X, Y, R, prm, pairs):
         c = scale * R[i] ** 2
         walls = [(0, X[i] - 0.0, 1.0, 0.0), (0, prm.nx - X[i], -1.0, 0.0),
                  (1, Y[i] - 0.0, 0.0, 1.0), (1, prm.ny - Y[i], 0.0, -1.0)]
+        ext = [R[i], R[i]]  # extent along x and along y
+        if semi_minor is not None and semi_minor[i] != R[i]:
+            a, b = R[i], semi_minor[i]
+            cth, sth = math.cos(theta[i]), math.sin(theta[i])
+            ext = [math.sqrt(a * a * cth * cth + b * b * sth * sth), math.sqrt(a * a * sth * sth + b * b * cth * cth)]
         for axis, dist, nxw, nyw in walls:
             if prm.periodic[axis]:
                 continue
+            if prm.outflow[2 * axis + (0 if (nxw > 0 or nyw > 0) else 1)]:
+                continue  # no wall on an open side
             d = 2.0 * dist
-            gap = 2.0 * R[i] + zeta - d
+            gap = 2.0 * ext[axis] + zeta - d
             if gap <= 0.0:
                 continue
             mag = (c / prm.contact_eps_w) * (gap / zeta) ** 2
@@ -627,6 +837,7 @@ class Params:
     contact_eps_p: float = 0.01
     contact_eps_w: float = 0.005
     periodic: tuple = (False, False)
+    outflow: tuple = (False, False, False, False)  # open sides x-, x+, y-, y+ (reading R14)
 
     # derived quantities (Sec. 3)
     @property
@@ -658,7 +869,7 @@ class Simulation:
     previous U, Omega and the hydrodynamic force and torque of level n."""
 
     def __init__(self, prm: Params, x, y, radius, T0, k_ratio=None, ux=None, uy=None, omega=None,
-                 fixed_T=None):
+                 fixed_T=None, semi_minor=None, theta=None):
         self.prm = prm
         n = len(x)
         z = np.zeros(n)
@@ -671,22 +882,33 @@ class Simulation:
             "ux": np.array(ux if ux is not None else z, dtype=float),
             "uy": np.array(uy if uy is not None else z, dtype=float),
             "omega": np.array(omega if omega is not None else z, dtype=float),
-            "theta": np.zeros(n),
+            "theta": np.array(theta if theta is not None else z, dtype=float),
         }
+        # semi-minor axes: an ellipse where it differs from the radius (the
+        # semi-major axis), a disk where it equals it (reading R13)
+        self.part["b"] = np.array(semi_minor if semi_minor is not None else radius, dtype=float)
         self.part["ux_prev"] = self.part["ux"].copy()
         self.part["uy_prev"] = self.part["uy"].copy()
         self.part["omega_prev"] = self.part["omega"].copy()
-        r = self.part["r"]
-        self.mass = prm.rho_ratio * math.pi * r * r           # M
-        self.inertia = 0.5 * self.mass * r * r                 # I_c (disk)
-        self.mass_in = 1.0 * math.pi * r * r                   # M_in = rho_f M / rho_s
-        self.inertia_in = 0.5 * self.mass_in * r * r           # I_c,in
+        self._set_inertia()
         self.S = flow_rates(prm.tau_f, prm.lambda_q_flow, prm.s_e)
         self.b = (-1.0 * prm.beta * prm.gravity[0], -1.0 * prm.beta * prm.gravity[1])
         self.step_count = 0
         self._init_state()
 
     # -- helpers ------------------------------------------------------------
+    def _set_inertia(self):
+        """Mass and moment of inertia of each particle and of its inside fluid
+        (Sec. 2.3): an ellipse of semi-axes a, b has area pi a b and polar
+        moment M (a^2 + b^2) / 4 (a disk: M R^2 / 2)."""
+        a, b = self.part["r"], self.part["b"]
+        area = math.pi * a * b
+        self.area = area
+        self.mass = self.prm.rho_ratio * area                  # M
+        self.inertia = 0.25 * self.mass * (a * a + b * b)      # I_c
+        self.mass_in = 1.0 * area                              # M_in = rho_f M / rho_s
+        self.inertia_in = 0.25 * self.mass_in * (a * a + b * b)  # I_c,in
+
     def _properties(self, ras: Raster):
         """c_v and lambda of Eq. 11, summed over owners."""
         p = self.prm
@@ -704,7 +926,10 @@ class Simulation:
 
     def _raster(self):
         p = self.prm
-        return rasterise(p.nx, p.ny, self.part["x"], self.part["y"], self.part["r"])
+        P = self.part
+        if (P["b"] != P["r"]).any():
+            return rasterise_shapes(p.nx, p.ny, P["x"], P["y"], P["r"], P["b"], P["theta"])
+        return rasterise(p.nx, p.ny, P["x"], P["y"], P["r"])
 
     def _init_state(self):
         """Initial state (reading R6)."""
@@ -745,8 +970,8 @@ class Simulation:
         p = self.prm
         P = self.part
         r = P["r"]
-        Fcon = contact_forces(P["x"], P["y"], r, p, self.pairs)
-        body = (p.rho_ratio - 1.0) * 1.0 * math.pi * r * r
+        Fcon = contact_forces(P["x"], P["y"], r, p, self.pairs, semi_minor=P["b"], theta=P["theta"])
+        body = (p.rho_ratio - 1.0) * 1.0 * self.area
         F_in_x = -self.mass_in * (P["ux"] - P["ux_prev"])
         F_in_y = -self.mass_in * (P["uy"] - P["uy_prev"])
         T_in = -self.inertia_in * (P["omega"] - P["omega_prev"])
@@ -780,14 +1005,11 @@ class Simulation:
                "omega": omega if omega is not None else z, "theta": z}
         for key, v in new.items():
             P[key] = np.concatenate([P[key], np.asarray(v, dtype=float)])
+        P["b"] = np.concatenate([P["b"], np.asarray(radius, dtype=float)])  # inserted particles are disks
         P["ux_prev"] = np.concatenate([P["ux_prev"], np.asarray(new["ux"], dtype=float)])
         P["uy_prev"] = np.concatenate([P["uy_prev"], np.asarray(new["uy"], dtype=float)])
         P["omega_prev"] = np.concatenate([P["omega_prev"], np.asarray(new["omega"], dtype=float)])
-        r = P["r"]
-        self.mass = self.prm.rho_ratio * math.pi * r * r
-        self.inertia = 0.5 * self.mass * r * r
-        self.mass_in = 1.0 * math.pi * r * r
-        self.inertia_in = 0.5 * self.mass_in * r * r
+        self._set_inertia()
         self.fixed_T = np.concatenate([self.fixed_T, np.zeros(n, dtype=bool)])
         self.F_mes = np.concatenate([self.F_mes, np.zeros((n, 2))])
         self.T_mes = np.concatenate([self.T_mes, z])
@@ -805,8 +1027,8 @@ class Simulation:
         Rd = thermal_rates(self.tau_g, p.thermal_rates_mode)
         gbar = collide_thermal(self.g, self.eps, self.T, self.qc, Rd, p.cref)
         # (2) streaming (Eqs. 3b, 17b)
-        fstar = stream_flow(fbar, p.periodic)
-        g = stream_thermal(gbar, p.cref, p.thermal_wall, p.wall_T, p.periodic)
+        fstar = stream_flow(fbar, p.periodic, p.outflow)
+        g = stream_thermal(gbar, p.cref, p.thermal_wall, p.wall_T, p.periodic, p.outflow)
         # (3) particle motion to level n+1 (reading R3), then f_s^{n+1}
         self._particle_update()
         fs_old = self.ras.fs
@@ -952,7 +1174,7 @@ def _min_image(d, L, periodic):
 class _RefHandle:
     def __init__(self, prm: Params):
         self.prm = prm
-        self.parts = {k: [] for k in ("x", "y", "r", "T0", "k", "ux", "uy", "omega", "fixed")}
+        self.parts = {k: [] for k in ("x", "y", "r", "T0", "k", "ux", "uy", "omega", "fixed", "b", "theta")}
         self.sim = None
         self.err = ""
 
@@ -993,6 +1215,29 @@ def vlbref_add_particles(h, n, xy, radius, T0, k_ratio=None, uv=None, omega=None
         P["uy"].append(float(uv[2 * k + 1]) if uv is not None else 0.0)
         P["omega"].append(float(omega[k]) if omega is not None else 0.0)
         P["fixed"].append(False)
+        P["b"].append(r)
+        P["theta"].append(0.0)
+    return VLBREF_OK
+
+
+def vlbref_add_ellipses(h, n, xy, semi_a, semi_b, theta, T0, k_ratio=None, uv=None, omega=None):
+    """Elliptical particles before the first step (reading R13): centres
+    xy[2n], semi-axes semi_a >= semi_b > 0, major-axis angles theta (radians
+    from the x axis), then as vlbref_add_particles.  A particle with
+    semi_a == semi_b is a disk.  VLBREF_EINVAL for a particle outside the walls
+    (judged by its circumscribed disk) or whose circumscribed disk overlaps
+    another's."""
+    xy = np.asarray(xy, dtype=float).reshape(-1)
+    for k in range(n):
+        if not (semi_a[k] >= semi_b[k] > 0.0):
+            return h.fail(VLBREF_EINVAL, "semi-axes must satisfy semi_a >= semi_b > 0")
+    n0 = len(h.parts["x"])
+    st = vlbref_add_particles(h, n, xy, semi_a, T0, k_ratio, uv, omega)
+    if st != VLBREF_OK:
+        return st
+    for k in range(n):
+        h.parts["b"][n0 + k] = float(semi_b[k])
+        h.parts["theta"][n0 + k] = float(theta[k])
     return VLBREF_OK
 
 
@@ -1011,7 +1256,7 @@ def _ensure(h):
     if h.sim is None:
         P = h.parts
         h.sim = Simulation(h.prm, P["x"], P["y"], P["r"], P["T0"], k_ratio=P["k"], ux=P["ux"], uy=P["uy"],
-                           omega=P["omega"], fixed_T=P["fixed"])
+                           omega=P["omega"], fixed_T=P["fixed"], semi_minor=P["b"], theta=P["theta"])
 
 
 def vlbref_insert_particles(h, n, xy, radius, T0, k_ratio=None, uv=None, omega=None):

@@ -1,12 +1,18 @@
 """What 16-bit population storage costs, measured on the oracle alone.
 
-The FP64 oracle is run twice on the settling-disk channel: once as it is, once
-with every post-collision population rounded to FP16 or BF16 (as the deviation
-from the rest equilibrium that the CUDA path stores) before streaming.  The
-u error of that rounding alone, over stacked snapshots of 1000 steps, already
-exceeds the 1e-3 bar of the reduced-precision parity check, so a CUDA path
-with 16-bit population storage cannot meet it whatever its arithmetic.  CPU
-only; about a minute and a half."""
+The FP64 oracle is run on the settling-disk channel as it is, and with every
+post-collision population rounded to FP16 or BF16 (as the deviation from the
+rest equilibrium that the CUDA path stores) before streaming, either to
+nearest or stochastically (up with probability equal to the distance from
+the lower neighbour; numpy's seeded generator stands in for the kernel's
+counter-based bits).  Round-to-nearest repeats the same error every step
+wherever the flow is steady, and the errors add up coherently through the
+exchange force; stochastic rounding leaves unbiased noise.  Over 500 steps
+(snapshots every 100): BF16 u 6.1e-3 to nearest against 2.3e-3
+stochastically, T 6.4e-4 against 7e-5; FP16 stochastically u 3.5e-4, T 9e-6,
+settling velocity 3e-5 (over 1000 steps: FP16 to nearest u 1.18e-3, which
+misses the 1e-3 bar, stochastically 3.5e-4).  CPU only; about two and a half
+minutes."""
 import numpy as np
 import pytest
 
@@ -16,18 +22,33 @@ from paper_2410_23802_gb300 import workloads as W
 
 pytestmark = pytest.mark.slow
 
-SNAP, NSNAP = 100, 10
+SNAP, NSNAP = 100, 5
 
 
-def _bf16(x):
-    """Round to BF16 (nearest even), returned as float64."""
+def _bf16_nearest(x, rng):
     b = x.astype(np.float32).view(np.uint32).astype(np.uint64)
     r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def _fp16(x):
-    return x.astype(np.float32).astype(np.float16).astype(np.float64)
+def _bf16_stochastic(x, rng):
+    """Add 16 random bits below the kept ones, then truncate: rounds up with
+    probability equal to the discarded fraction."""
+    b = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + rng.integers(0, 1 << 16, size=b.shape, dtype=np.uint64)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _fp16_stochastic(x, rng):
+    """Between the two FP16 neighbours of x, the upper one with probability
+    (x - lower) / (upper - lower)."""
+    a = x.astype(np.float32).astype(np.float16)
+    a64 = a.astype(np.float64)
+    other = np.where(a64 > x, np.nextafter(a, np.float16(-np.inf)),
+                     np.nextafter(a, np.float16(np.inf))).astype(np.float64)
+    lo, hi = np.minimum(a64, other), np.maximum(a64, other)
+    p = np.where(hi > lo, (x - lo) / np.where(hi > lo, hi - lo, 1.0), 0.0)
+    return np.where(a64 == x, a64, np.where(rng.random(size=x.shape) < p, hi, lo))
 
 
 def _snapshots(sim):
@@ -35,7 +56,7 @@ def _snapshots(sim):
     for _ in range(NSNAP):
         sim.step(SNAP)
         f = sim.fields()
-        out.append((np.stack([f["ux"], f["uy"]]), f["T"].copy()))
+        out.append((np.stack([f["ux"], f["uy"]]), f["T"].copy(), float(sim.particle_state()["uy"][0])))
     return out
 
 
@@ -44,19 +65,40 @@ def exact():
     return _snapshots(oracle_sim(W.channel()))
 
 
-@pytest.mark.parametrize("name,rnd,u_min", [("fp16", _fp16, 1e-3), ("bf16", _bf16, 1e-2)])
-def test_storage_rounding_alone_misses_the_bar(exact, monkeypatch, name, rnd, u_min):
-    case = W.channel()
-    sim = oracle_sim(case)
+_cache = {}
+
+
+def _rounded(exact, rnd):
+    if rnd in _cache:
+        return _cache[rnd]
+    sim = oracle_sim(W.channel())
     p = sim.prm
     w = O.feq(np.ones((1, 1)), np.zeros((1, 1)), np.zeros((1, 1)))
     g_rest = O.geq(np.full((1, 1), p.T_fluid_init * 1.0), np.full((1, 1), p.T_fluid_init), p.cref)
     collide_f, collide_g = O.collide_flow, O.collide_thermal
-    monkeypatch.setattr(O, "collide_flow", lambda *a: w + rnd(collide_f(*a) - w))
-    monkeypatch.setattr(O, "collide_thermal", lambda *a: g_rest + rnd(collide_g(*a) - g_rest))
-    rounded = _snapshots(sim)
-    e_u = rel_l2(np.stack([r[0] for r in rounded]), np.stack([e[0] for e in exact]))
-    e_T = rel_l2(np.stack([r[1] for r in rounded]), np.stack([e[1] for e in exact]))
-    print(f"{name}: u {e_u:.3e}  T {e_T:.3e}")
-    assert u_min < e_u < 10 * u_min, e_u
-    assert e_T < e_u
+    rng = np.random.default_rng(2024)
+    mp = pytest.MonkeyPatch()
+    mp.setattr(O, "collide_flow", lambda *a: w + rnd(collide_f(*a) - w, rng))
+    mp.setattr(O, "collide_thermal", lambda *a: g_rest + rnd(collide_g(*a) - g_rest, rng))
+    try:
+        got = _snapshots(sim)
+    finally:
+        mp.undo()
+    e = {"u": rel_l2(np.stack([r[0] for r in got]), np.stack([x[0] for x in exact])),
+         "T": rel_l2(np.stack([r[1] for r in got]), np.stack([x[1] for x in exact])),
+         "v": abs(got[-1][2] - exact[-1][2]) / abs(exact[-1][2])}
+    print(rnd.__name__, {k: f"{v:.3e}" for k, v in e.items()})
+    _cache[rnd] = e
+    return e
+
+
+def test_stochastic_rounding_removes_the_bias_of_bf16_storage(exact):
+    near = _rounded(exact, _bf16_nearest)
+    sto = _rounded(exact, _bf16_stochastic)
+    assert near["u"] > 4e-3 and sto["u"] < 0.5 * near["u"]
+    assert sto["T"] < 0.2 * near["T"] and sto["v"] < 0.2 * near["v"]
+
+
+def test_fp16_storage_rounded_stochastically_meets_the_bar(exact):
+    e = _rounded(exact, _fp16_stochastic)
+    assert e["u"] < 1e-3 and e["T"] < 1e-3 and e["v"] < 1e-2
