@@ -82,7 +82,11 @@ enum {
  * vlb_params_default() and override fields.  Walls sit on the cell faces of
  * every non-periodic side; they are no-slip (halfway bounce-back of f) and
  * either adiabatic (bounce-back of g) or held at wall_T (anti-bounce-back).
- * Side order in the [4] arrays: x-, x+, y-, y+.
+ * A side whose bit is set in outflow_mask is open instead: the fully
+ * developed condition of Sec. 3.2 (zero normal derivative), read as a
+ * population entering there taking the value the same population has one
+ * cell further in, for f and g; no wall contact there.
+ * Side order in the [4] arrays and the mask bits: x-, x+, y-, y+.
  */
 typedef struct {
   uint32_t abi_version;       /* must equal VLB_ABI_VERSION */
@@ -92,7 +96,8 @@ typedef struct {
   int32_t thermal_rates_mode; /* 0: (1/s_j-1/2)(1/s_e-1/2)=1/4 (Sec. 3); 1: s_0=s_e=s_eps=1 (Sec. 3.5) */
   int32_t precision;          /* vlb_precision */
   int32_t max_particles;      /* capacity of the particle arrays */
-  int32_t reserved0, reserved1;  /* zero */
+  int32_t outflow_mask;       /* bit k set: side k is open (outflow); 0: every side is a wall */
+  int32_t reserved1;          /* zero */
   double tau_f;               /* flow relaxation time, s_p = 1/tau_f (Sec. 2.1) */
   double lambda_q_flow;       /* (1/s_p-1/2)(1/s_q-1/2); the paper uses 1/12 (Sec. 3) */
   double s_e;                 /* s_e = s_eps; the paper uses 1.25 (Sec. 3) */
@@ -151,6 +156,24 @@ vlb_status vlb_set_stream(vlb_handle* h, void* cuda_stream);
 vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const double* radius,
                              const double* T0, const double* k_ratio, const double* uv,
                              const double* omega);
+
+/* Append n elliptical particles (Sec. 3.2) before the first step: centres
+ * xy[2n], semi-axes semi_a[n] >= semi_b[n] >= 1 lu, theta[n] the angle of
+ * the major axis from the x axis (radians), then as vlb_add_particles.
+ * Reading of the paper (silent on all of it): the solid fraction is the
+ * exact area of ellipse and cell; a cell is solid when its four corners lie
+ * in the ellipse and fluid when the ellipse's quadratic form stays >= 1
+ * over it, both decided in FP64; the orientation advances with the angular
+ * velocity (theta + Omega per step, forward Euler) and sets the raster; mass
+ * rho_s pi a b, moment of inertia M (a^2 + b^2) / 4; between particles the
+ * contact force acts on the circumscribed disks (radius semi_a), at a wall
+ * on the ellipse's extent along the wall's normal.  A particle with
+ * semi_a == semi_b is a disk.  Errors as vlb_add_particles (the domain and
+ * overlap tests use the circumscribed disks), VLB_EINVAL for semi-axes out
+ * of order or below 1. */
+vlb_status vlb_add_ellipses(vlb_handle* h, int32_t n, const double* xy, const double* semi_a,
+                            const double* semi_b, const double* theta, const double* T0,
+                            const double* k_ratio, const double* uv, const double* omega);
 
 /* Add n disks between two steps (mid-run insertion; before the first step
  * the same as vlb_add_particles).  Reading (the paper has no insertion): a

@@ -48,6 +48,7 @@ struct vlb_handle {
   // particles
   int np = 0, cap = 0;
   std::vector<double> hx, hy, hr, hT0, hk, hux, huy, hom;
+  std::vector<double> hrb, hth;  // semi-minor axes (= hr for disks) and initial angles (reading R13)
   std::vector<int> hfix;  // particles held at their temperature
   ParticleArrays P{};
   TileLists TL[2] = {};
@@ -158,6 +159,7 @@ static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
   K.nx = h->nx; K.ny = h->ny; K.pitch = h->pitch; K.ntx = h->ntx; K.nty = h->nty;
   K.plane = h->plane;
   K.per_x = p.periodic[0]; K.per_y = p.periodic[1];
+  for (int w = 0; w < 4; ++w) K.outflow[w] = (p.outflow_mask >> w) & 1;
   for (int w = 0; w < 4; ++w) {
     K.wall_dirichlet[w] = p.thermal_wall[w] == VLB_WALL_DIRICHLET;
     K.wall_dT[w] = C(p.wall_T[w] - p.T_fluid_init);
@@ -242,6 +244,9 @@ static const char* params_error(const vlb_params& p) {
     if (p.periodic[k] != 0 && p.periodic[k] != 1) return "periodic must be 0/1";
   for (int w = 0; w < 4; ++w)
     if (p.thermal_wall[w] != 0 && p.thermal_wall[w] != 1) return "thermal_wall";
+  if (p.outflow_mask & ~0xF) return "outflow_mask has bits beyond the four sides";
+  for (int w = 0; w < 4; ++w)
+    if (((p.outflow_mask >> w) & 1) && p.periodic[w / 2]) return "an open (outflow) side on a periodic axis";
   return nullptr;
 }
 
@@ -271,10 +276,10 @@ static double min_image(double d, int L, int periodic) {
   if (d < -0.5 * L) return d + L;
   return d;
 }
-// The particle block: 15 doubles, one int4, NBR_CAP + 2 ints, 8 doubles and
+// The particle block: 16 doubles, one int4, NBR_CAP + 2 ints, 8 doubles and
 // one raster record per particle, every sub-array on a 256-byte boundary.
 static size_t particle_block_bytes(size_t capn) {
-  return 15 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) + a256(capn * sizeof(int)) +
+  return 16 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) + a256(capn * sizeof(int)) +
          a256(capn * NBR_CAP * sizeof(int)) + a256(capn * sizeof(int)) + a256(capn * 8 * sizeof(double)) +
          a256(capn * sizeof(RasterRec));
 }
@@ -359,10 +364,10 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   h->pbytes = pbytes;
   {
     char* b = static_cast<char*>(h->pbase);
-    double** d[15] = {&h->P.x, &h->P.y, &h->P.theta, &h->P.ux, &h->P.uy, &h->P.om, &h->P.ux_prev,
+    double** d[16] = {&h->P.x, &h->P.y, &h->P.theta, &h->P.ux, &h->P.uy, &h->P.om, &h->P.ux_prev,
                       &h->P.uy_prev, &h->P.om_prev, &h->P.fcx, &h->P.fcy, &h->P.tc, &h->P.r,
-                      &h->P.lam_s, &h->P.T0};
-    for (int k = 0; k < 15; ++k) { *d[k] = reinterpret_cast<double*>(b); b += a256(capn * sizeof(double)); }
+                      &h->P.lam_s, &h->P.T0, &h->P.rb};
+    for (int k = 0; k < 16; ++k) { *d[k] = reinterpret_cast<double*>(b); b += a256(capn * sizeof(double)); }
     h->P.prange = reinterpret_cast<int4*>(b); b += a256(capn * sizeof(int4));
     h->P.nbr_count = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.nbr = reinterpret_cast<int*>(b); b += a256(capn * NBR_CAP * sizeof(int));
@@ -448,6 +453,8 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
     h->hx.push_back(xy[2 * k]);
     h->hy.push_back(xy[2 * k + 1]);
     h->hr.push_back(radius[k]);
+    h->hrb.push_back(radius[k]);
+    h->hth.push_back(0.0);
     h->hT0.push_back(T0[k]);
     h->hk.push_back(k_ratio ? k_ratio[k] : p.k_ratio_default);
     h->hfix.push_back(0);
@@ -459,6 +466,25 @@ vlb_status vlb_add_particles(vlb_handle* h, int32_t n, const double* xy, const d
   return VLB_OK;
 }
 
+
+vlb_status vlb_add_ellipses(vlb_handle* h, int32_t n, const double* xy, const double* semi_a, const double* semi_b,
+                            const double* theta, const double* T0, const double* k_ratio, const double* uv,
+                            const double* omega) {
+  if (!h) return VLB_EINVAL;
+  if (n < 0 || (n > 0 && (!semi_a || !semi_b || !theta))) return fail(h, VLB_EINVAL, "bad ellipse arrays");
+  for (int k = 0; k < n; ++k)
+    if (!(semi_b[k] >= 1.0 && semi_a[k] >= semi_b[k]) || !std::isfinite(theta[k]))
+      return fail(h, VLB_EINVAL, "ellipse semi-axes must satisfy semi_a >= semi_b >= 1 and theta be finite");
+  const int n0 = h->np;
+  // the circumscribed disks go through the disks' checks (domain, overlap)
+  const vlb_status st = vlb_add_particles(h, n, xy, semi_a, T0, k_ratio, uv, omega);
+  if (st != VLB_OK) return st;
+  for (int k = 0; k < n; ++k) {
+    h->hrb[n0 + k] = semi_b[k];
+    h->hth[n0 + k] = theta[k];
+  }
+  return VLB_OK;
+}
 
 // Lattice pass with list buffer `lists`; STEP and INIT also clear the other
 // list buffer for the next particle step.
@@ -500,15 +526,17 @@ static vlb_status upload_particles(vlb_handle* h, int first, int count) {
   const double cscale = std::fabs(p.rho_ratio - 1.0) * gmag * M_PI;
   for (int k = 0; k < count; ++k) {
     lam[k] = h->hk[first + k] * lam_f;
-    const double R = h->hr[first + k], area = M_PI * R * R;
-    const double M = p.rho_ratio * area, I = 0.5 * M * R * R;
+    // an ellipse of semi-axes a >= b (a disk: a = b = R): area pi a b, polar
+    // moment M (a^2 + b^2) / 4 (reading R13)
+    const double a = h->hr[first + k], b = h->hrb[first + k], area = M_PI * a * b;
+    const double M = p.rho_ratio * area, I = 0.25 * M * (a * a + b * b);
     double* q = pk.data() + 8 * (size_t)k;
     q[0] = 1.0 / M;
     q[1] = 1.0 / I;
-    q[2] = area;                // M_in = rho_f M / rho_s
-    q[3] = 0.5 * area * R * R;  // I_in
+    q[2] = area;                            // M_in = rho_f M / rho_s
+    q[3] = 0.25 * area * (a * a + b * b);   // I_in
     q[4] = (p.rho_ratio - 1.0) * area;
-    q[5] = cscale * R * R / p.contact_eps_w;
+    q[5] = cscale * a * a / p.contact_eps_w;
   }
   const size_t b = count * sizeof(double);
   auto up = [&](double* dst, const double* src) {
@@ -517,6 +545,8 @@ static vlb_status upload_particles(vlb_handle* h, int first, int count) {
   CK(h, up(h->P.x, h->hx.data() + first));
   CK(h, up(h->P.y, h->hy.data() + first));
   CK(h, up(h->P.r, h->hr.data() + first));
+  CK(h, up(h->P.rb, h->hrb.data() + first));
+  CK(h, up(h->P.theta, h->hth.data() + first));
   CK(h, up(h->P.T0, h->hT0.data() + first));
   CK(h, up(h->P.lam_s, lam.data()));
   CK(h, cudaMemcpyAsync(h->P.fixed_T + first, h->hfix.data() + first, count * sizeof(int), cudaMemcpyHostToDevice,
@@ -561,12 +591,15 @@ static vlb_status initialize(vlb_handle* h) {
 
   ParticleConst& c = h->PC;
   c.np = n; c.nx = h->nx; c.ny = h->ny; c.per_x = p.periodic[0]; c.per_y = p.periodic[1];
+  for (int w = 0; w < 4; ++w) c.outflow[w] = (p.outflow_mask >> w) & 1;
   c.ntx = h->ntx; c.nty = h->nty;
   c.band_off = band_off;
   h->K32.band_off = h->K64.band_off = band_off;
   int any_held = 0;
   for (int v : h->hfix) any_held |= v;
   h->K32.any_held = h->K64.any_held = any_held;
+  c.any_ellipse = 0;
+  for (size_t k = 0; k < h->hr.size(); ++k) c.any_ellipse |= h->hrb[k] != h->hr[k];
   c.rho_ratio = p.rho_ratio; c.gx = p.gravity[0]; c.gy = p.gravity[1];
   c.zeta = p.contact_range; c.eps_p = p.contact_eps_p; c.eps_w = p.contact_eps_w;
   c.contact_scale = std::fabs(p.rho_ratio - 1.0) * std::hypot(p.gravity[0], p.gravity[1]) * M_PI;
@@ -654,6 +687,8 @@ vlb_status vlb_insert_particles(vlb_handle* h, int32_t n, const double* xy, cons
     h->hx.push_back(xy[2 * k]);
     h->hy.push_back(xy[2 * k + 1]);
     h->hr.push_back(radius[k]);
+    h->hrb.push_back(radius[k]);
+    h->hth.push_back(0.0);
     h->hT0.push_back(T0[k]);
     h->hk.push_back(k_ratio ? k_ratio[k] : p.k_ratio_default);
     h->hfix.push_back(0);
@@ -846,8 +881,10 @@ vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int3
   const auto* d_part = reinterpret_cast<const BatchParticles*>(dev);
   const auto* d_items = reinterpret_cast<const int2*>(dev + items_off);
   const int nitems = (int)items.size();
+  bool any_ellipse = false;
+  for (int i = 0; i < n; ++i) any_ellipse |= hs[i]->PC.any_ellipse != 0;
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
-    e = launch_particle_step_batch(d_part, d_items, nitems, k, bs);
+    e = launch_particle_step_batch(d_part, d_items, nitems, k, any_ellipse, bs);
     for (auto& g : groups) {
       if (e != cudaSuccess) break;
       const int* table = reinterpret_cast<const int*>(dev + g.table_off);
@@ -1216,11 +1253,17 @@ vlb_status vlb_load_state(vlb_handle* h, const void* buf, uint64_t bytes) {
     CK(h, put(h->TL[b].count, I.tl_count_bytes));
     CK(h, put(h->TL[b].ids, I.tl_ids_bytes));
   }
-  // the held-temperature flags came with the particle block
-  if (h->np > 0) CK(h, cudaMemcpy(h->hfix.data(), h->P.fixed_T, h->np * sizeof(int), cudaMemcpyDeviceToHost));
+  // the held-temperature flags and the ellipses' axes came with the particle block
+  if (h->np > 0) {
+    CK(h, cudaMemcpy(h->hfix.data(), h->P.fixed_T, h->np * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(h->hrb.data(), h->P.rb, h->np * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(h->hr.data(), h->P.r, h->np * sizeof(double), cudaMemcpyDeviceToHost));
+  }
   int any_held = 0;
   for (int v : h->hfix) any_held |= v;
   h->K32.any_held = h->K64.any_held = any_held;
+  h->PC.any_ellipse = 0;
+  for (int k = 0; k < h->np; ++k) h->PC.any_ellipse |= h->hrb[k] != h->hr[k];
   h->cur = I.cur;
   h->tl = I.tl;
   h->step = I.step;
@@ -1257,8 +1300,8 @@ vlb_status vlb_profile_end(vlb_handle* h, double* lattice_ms, int32_t* lattice_l
   }
   if (lattice_ms) *lattice_ms = tot;
   if (lattice_launches) *lattice_launches = h->ev_used / 2;
-  // particle_step and the lattice kernel
-  if (launches_per_step) *launches_per_step = h->np > 0 ? 2 : 1;
+  // particle_step (and the ellipses' band pass) and the lattice kernel
+  if (launches_per_step) *launches_per_step = h->np > 0 ? (h->PC.any_ellipse ? 3 : 2) : 1;
   h->prof = false;
   h->ev_used = 0;
   return VLB_OK;

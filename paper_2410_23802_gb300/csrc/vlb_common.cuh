@@ -84,7 +84,8 @@ struct ParticleArrays {
   double *x, *y, *theta, *ux, *uy, *om;
   double *ux_prev, *uy_prev, *om_prev;
   double *fcx, *fcy, *tc;  // F_c, T_c of the last update
-  double *r, *lam_s, *T0;  // radius, lambda_s, initial temperature
+  double *r, *lam_s, *T0;  // radius (an ellipse's semi-major axis), lambda_s, initial temperature
+  double* rb;              // semi-minor axis (equal to r for a disk; reading R13)
   int4* prange;            // tile range (tx0, ty0, ntx, nty) at the current level
   unsigned long long* mes; // [n][3][2] F_MES,x + contact x, F_MES,y + contact y, T_MES as fixed point (mes_add)
   int* nbr_count;          // contact partners per particle
@@ -157,6 +158,7 @@ struct LatticeConst {
   int any_held;            // some particle is held at its temperature (reading R11)
   int pf_tiles;            // L2 prefetch distance in tiles (0: none), see prefetch_ahead
   int wall_dirichlet[4];   // x-, x+, y-, y+
+  int outflow[4];          // open sides (zero normal gradient; reading R14)
   int np;
   double zeta;             // contact range
   double contact_scale;    // |rho_r - 1| rho_f |g| pi

@@ -8,6 +8,8 @@ namespace vlb {
 // Constants of the particle kernels (Sec. 2.3 and the contact model).
 struct ParticleConst {
   int np, nx, ny, per_x, per_y, ntx, nty;
+  int outflow[4];    // open sides (no wall contact there)
+  int any_ellipse;   // some particle is an ellipse (its band pass runs in a kernel of its own)
   int band_off;      // half-width of the band tables (cells)
   int band_stamp;    // level stamp written into the band tables
   double rho_ratio, gx, gy;
@@ -71,7 +73,7 @@ cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P
 cudaError_t launch_particle_step(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
                                  cudaStream_t st);
 cudaError_t launch_particle_step_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
-                                       cudaStream_t st);
+                                       bool any_ellipse, cudaStream_t st);
 
 // Batched step k: lattice tiles map to their case through tile_case.
 // `held`: the held-temperature path (every case of the launch shares

@@ -164,9 +164,14 @@ __device__ int load_tile_particles(const LatticeConst<C>& K, const ParticleArray
       q.rq2 = rq * rq;
       q.xh = C(X); q.xl = C(X - double(q.xh));
       q.yh = C(Y); q.yl = C(Y - double(q.yh));
+      const double Rb = P.rb[id];
       q.r = C(R);
       q.far2 = C((R + 0.75) * (R + 0.75));
-      q.near2 = R > 0.75 ? C((R - 0.75) * (R - 0.75)) : C(-1);
+      q.near2 = Rb > 0.75 ? C((Rb - 0.75) * (Rb - 0.75)) : C(-1);
+      q.ell = Rb != R;  // an ellipse: semi-axes R >= Rb (reading R13)
+      q.ex = P.x[id]; q.ey = P.y[id]; q.ea = R; q.eb = Rb;
+      q.ec = 1.0; q.es = 0.0;
+      if (q.ell) sincos(P.theta[id], &q.es, &q.ec);
       q.ux = C(P.ux[id]); q.uy = C(P.uy[id]); q.om = C(P.om[id]);
       q.uxl = C(P.ux[id] - double(q.ux)); q.uyl = C(P.uy[id] - double(q.uy));
       q.lam_s = C(P.lam_s[id]); q.T0 = C(P.T0[id]);
@@ -221,7 +226,7 @@ __device__ __forceinline__ C raster_cell(int tx, int ty, int gx, int gy, int np,
         if (c == CELL_FLUID) continue;
       }
     } else {
-      c = cell_fraction(tx, ty, s_p[s], f);
+      c = s_p[s].ell ? ellipse_cell_fraction(tx, ty, gx, gy, s_p[s], f) : cell_fraction(tx, ty, s_p[s], f);
       if (c == CELL_FLUID) continue;
     }
     if (nown == MAX_OWNERS) { atomicOr(err, ERR_OWNER_OVERFLOW); break; }
@@ -323,17 +328,23 @@ __device__ __forceinline__ void pull_direct(const LatticeConst<C>& K, const Step
       else outx = sx < 0 || sx >= K.nx;
       if (K.per_y) sy = sy < 0 ? sy + K.ny : (sy >= K.ny ? sy - K.ny : sy);
       else outy = sy < 0 || sy >= K.ny;
-      if (!(outx || outy)) {
-        const long long sc = (long long)sy * K.pitch + sx;
+      // an open side (reading R14): the population takes the value of the
+      // same population one cell further in, i.e. the source moved back
+      // across the side(s) it crossed
+      const bool openx = outx && K.outflow[sx < 0 ? 0 : 1];
+      const bool openy = outy && K.outflow[sy < 0 ? 2 : 3];
+      if (!(outx || outy) || (openx && openy) || (openx && !outy) || (openy && !outx)) {
+        const long long sc = (long long)(outy ? y : sy) * K.pitch + (outx ? x : sx);
         f[i] = load_pop<C>(src + (long long)i * K.plane + sc);
         g[i] = load_pop<C>(src + (long long)(9 + i) * K.plane + sc);
       } else {
         // halfway bounce-back of f; g bounces back (adiabatic) or anti-bounces
-        // back to the wall temperature; corners go to the y wall
+        // back to the wall temperature; corners go to the y wall (to the x
+        // wall when the y side is open)
         f[i] = load_pop<C>(src + (long long)opp(i) * K.plane + cell);
         // (deviations: g^eq_i(T_w) - g^eq_i(T_f) = w_i c_ref (T_w - T_f) for i >= 1)
         const C gb = load_pop<C>(src + (long long)(9 + opp(i)) * K.plane + cell);
-        const int wall = outy ? (sy < 0 ? 2 : 3) : (sx < 0 ? 0 : 1);
+        const int wall = (outy && !openy) ? (sy < 0 ? 2 : 3) : (sx < 0 ? 0 : 1);
         g[i] = K.wall_dirichlet[wall] ? (C(2) * wgt<C>(i) * K.cref * K.wall_dT[wall] - gb) : gb;
       }
     }

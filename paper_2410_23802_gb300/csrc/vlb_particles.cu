@@ -1,14 +1,16 @@
 // Particle kernels (Sec. 2.3).
 //
-//   particle_advance (thread per particle, FP64): F_MES, T_MES of Eq. 28 from
-//     the integer accumulators the lattice kernel filled (then cleared); the
-//     inside-fluid force and torque of Eq. 29 with backward differences; the
-//     short-range contact force; Eqs. 26 and 30 by forward Euler; the raster
-//     record and the tile range of the new position;
-//   particle_band_cta (CTA per particle, FP32): appends the particle to the
-//     tile lists of its range (the lattice kernel ranks each list by id and
-//     finds the contact partners of the level) and fills its band table.
-//   particle_range, then particle_band_cta: the same for the initial state.
+//   particle_step (one launch per time step): for each particle
+//     advance (one lane, FP64): F_MES, T_MES of Eq. 28 from the integer
+//       accumulators the lattice kernel filled (then cleared); the
+//       inside-fluid force and torque of Eq. 29 with backward differences;
+//       the short-range contact force; Eqs. 26 and 30 by forward Euler; the
+//       raster record and the tile range of the new position;
+//     band pass (one warp): appends the particle to the tile lists of its
+//       range (the lattice kernel ranks each list by id and finds the
+//       contact partners of the level) and fills its band table (FP32 for a
+//       disk, FP64 for an ellipse).
+//   particle_range, particle_band: the same for the initial state.
 #include <math.h>
 
 #include "vlb_common.cuh"
@@ -40,8 +42,10 @@ __device__ __forceinline__ void check_domain(const ParticleConst& c, double X, d
   if (bad) atomicOr(err, ERR_OUT_OF_DOMAIN);
 }
 
-// Raster record of particle p at centre (X, Y) with velocity (ux, uy, om).
-__device__ __forceinline__ void write_record(const ParticleArrays& P, int p, double X, double Y, double R,
+// Raster record of particle p at centre (X, Y) with velocity (ux, uy, om);
+// R its radius (an ellipse's semi-major axis), Rb its semi-minor axis: the
+// quick test's bounds are the circumscribed and inscribed circles.
+__device__ __forceinline__ void write_record(const ParticleArrays& P, int p, double X, double Y, double R, double Rb,
                                              double ux, double uy, double om, float lam_s, float T0) {
   RasterRec q;
   const double Q = double(1 << QBITS);
@@ -56,7 +60,7 @@ __device__ __forceinline__ void write_record(const ParticleArrays& P, int p, dou
   q.yfh = float(fy); q.yfl = float(fy - double(q.yfh));
   q.r = float(R);
   q.far2 = float((R + 0.75) * (R + 0.75));
-  q.near2 = R > 0.75 ? float((R - 0.75) * (R - 0.75)) : -1.0f;
+  q.near2 = Rb > 0.75 ? float((Rb - 0.75) * (Rb - 0.75)) : -1.0f;
   q.ux = float(ux); q.uxl = float(ux - double(q.ux));
   q.uy = float(uy); q.uyl = float(uy - double(q.uy));
   q.om = float(om);
@@ -70,12 +74,12 @@ __global__ void particle_range_kernel(const ParticleConst c, const ParticleArray
   if (p >= c.np) return;
   const int4 rg = tile_range(c, P.x[p], P.y[p], P.r[p]);
   P.prange[p] = rg;
-  write_record(P, p, P.x[p], P.y[p], P.r[p], P.ux[p], P.uy[p], P.om[p], float(P.lam_s[p]), float(P.T0[p]));
+  write_record(P, p, P.x[p], P.y[p], P.r[p], P.rb[p], P.ux[p], P.uy[p], P.om[p], float(P.lam_s[p]), float(P.T0[p]));
 }
 
 // Particle p's update (one thread).
 __device__ __forceinline__ void advance_one(const ParticleConst& c, const ParticleArrays& P, int p, unsigned* err) {
-  const double X = P.x[p], Y = P.y[p], R = P.r[p];
+  const double X = P.x[p], Y = P.y[p], R = P.r[p], Rb = P.rb[p];
   const double ux = P.ux[p], uy = P.uy[p], om = P.om[p];
   const double* kp = P.pk + 8 * p;  // 1/M, 1/I, M_in, I_in, body factor, wall factor
   double k[6];
@@ -96,14 +100,22 @@ __device__ __forceinline__ void advance_one(const ParticleConst& c, const Partic
   reinterpret_cast<ulonglong2*>(acc)[1] = make_ulonglong2(0ull, 0ull);
   reinterpret_cast<ulonglong2*>(acc)[2] = make_ulonglong2(0ull, 0ull);
   P.nbr_count[p] = 0;  // the lattice kernel of this step lists the next partners
-  // wall contact forces: walls x-, x+, y-, y+
+  // wall contact forces: walls x-, x+, y-, y+ (none on open sides); an
+  // ellipse meets a wall with its extent along the wall's normal (reading R13)
   double Fc_x = 0.0, Fc_y = 0.0;
   {
     const double dist[4] = {X, double(c.nx) - X, Y, double(c.ny) - Y};
     const double nxw[4] = {1.0, -1.0, 0.0, 0.0}, nyw[4] = {0.0, 0.0, 1.0, -1.0};
+    double ext_x = R, ext_y = R;
+    if (Rb != R) {
+      double sn, cs;
+      sincos(theta, &sn, &cs);
+      ext_x = sqrt(R * R * cs * cs + Rb * Rb * sn * sn);
+      ext_y = sqrt(R * R * sn * sn + Rb * Rb * cs * cs);
+    }
     for (int w = 0; w < 4; ++w) {
-      if ((w < 2 && c.per_x) || (w >= 2 && c.per_y)) continue;
-      const double gap = 2.0 * R + c.zeta - 2.0 * dist[w];
+      if ((w < 2 && c.per_x) || (w >= 2 && c.per_y) || c.outflow[w]) continue;
+      const double gap = 2.0 * (w < 2 ? ext_x : ext_y) + c.zeta - 2.0 * dist[w];
       if (gap <= 0.0) continue;
       const double gz = gap * c.inv_zeta;
       const double mag = k[5] * gz * gz;
@@ -136,7 +148,7 @@ __device__ __forceinline__ void advance_one(const ParticleConst& c, const Partic
   P.om[p] = omn;
   if (!(uxn * uxn + uyn * uyn <= 0.25)) atomicOr(err, ERR_TOO_FAST);
   check_domain(c, Xn, Yn, R, err);
-  write_record(P, p, Xn, Yn, R, uxn, uyn, omn, lam_s, T0);
+  write_record(P, p, Xn, Yn, R, Rb, uxn, uyn, omn, lam_s, T0);
   const int4 nr = tile_range(c, Xn, Yn, R);
   P.prange[p] = nr;
   // (the band kernel that follows appends the particle to the tile lists)
@@ -147,27 +159,57 @@ __device__ __forceinline__ void advance_one(const ParticleConst& c, const Partic
 // leaves open.  Results go to the particle's band table with the level's
 // stamp; the geometry (tile_geometry) and the tests are the ones the lattice
 // kernel itself uses, so the results are the ones it would compute.
-// The band pass of one particle by a whole CTA (BAND_CTA threads), the form
-// the time step uses: the particle's tile-list appends one thread per tile,
-// the quick test of every cell of its box spread over the threads, the band
-// cells queued in shared memory, then their exact class and area one thread
-// per cell.  The box is taken in chunks of BAND_CHUNK cells per thread, so
-// the queue (at most BAND_CTA * BAND_CHUNK cells) never overflows.  Same
-// geometry and tests as band_one, so the same table entries.
-constexpr int BAND_CTA = 128;
-constexpr int BAND_CHUNK = 8;
+constexpr int BAND_WARPS = 4;    // particles per CTA
+constexpr int BAND_QUEUE = 256;  // queued band cells per warp before an evaluation pass
 
-__device__ __forceinline__ void band_cta(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
-                                         unsigned* err, int p, int stamp) {
-  __shared__ int s_queue[BAND_CTA * BAND_CHUNK];
-  __shared__ int s_nq;
-  const int tid = threadIdx.x;
+// ELL: the band pass of an ellipse (its exact classes and areas in FP64),
+// compiled into a kernel of its own so that the disk path keeps its
+// register budget.
+template <bool ELL>
+__device__ __forceinline__ void band_evaluate(const ParticleConst& c, const ParticleArrays& P, int p, int stamp,
+                                              const RasterRec& rc, int bw, const int* queue, int nq, int lane) {
+  // an ellipse: its exact classes and areas in FP64 at the level's position
+  // and angle (reading R13); a disk: the FP32 geometry of the lattice kernel
+  double ea = 0.0, eb = 0.0, ex = 0.0, ey = 0.0, ec = 1.0, es = 0.0;
+  if (ELL && nq > 0) {
+    ea = P.r[p];
+    eb = P.rb[p];
+    ex = P.x[p];
+    ey = P.y[p];
+    sincos(P.theta[p], &es, &ec);
+  }
+  for (int j = lane; j < nq; j += 32) {
+    const int k = queue[j];
+    const int by = k / bw, bx = k - by * bw;
+    const int x = rc.xi - c.band_off + bx, y = rc.yi - c.band_off + by;
+    float f;
+    int cls;
+    if constexpr (ELL) {
+      cls = ellipse_cell_class(x, y, ex, ey, ea, eb, ec, es);
+      const double ar = cls == CELL_SOLID ? 1.0 : (cls == CELL_FLUID ? 0.0 : ellipse_cell_area(x, y, ex, ey, ea, eb, ec, es));
+      f = float(ar < 0.0 ? 0.0 : (ar > 1.0 ? 1.0 : ar));
+    } else {
+      const int x0 = x - x % TILE_X, y0 = y - y % TILE_Y;
+      PartTile<float> q;
+      tile_geometry(rc, x0, y0, q);
+      cls = cell_fraction(x - x0, y - y0, q, f);
+    }
+    P.band[(long long)p * bw * bw + k] = make_int2(cls | (stamp << 2), __float_as_int(f));
+  }
+}
+
+// Particle p's lists and band table (one warp; queue: BAND_QUEUE ints of
+// shared memory of this warp).
+template <bool ELL>
+__device__ __forceinline__ void band_one(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL,
+                                         unsigned* err, int p, int stamp, int* queue, int lane) {
   const RasterRec rc = P.rec[p];
   const int bw = 2 * c.band_off + 1;
+  // append the particle to the lists of the tiles of its range, one lane per tile
   {
     const int4 rg = P.prange[p];
     const int n = rg.z * rg.w;
-    for (int t = tid; t < n; t += BAND_CTA) {
+    for (int t = lane; t < n; t += 32) {
       const int ty = t / rg.z, tx = t - ty * rg.z;
       const int tile = (rg.y + ty) * c.ntx + (rg.x + tx);
       const int slot = atomicAdd(&TL.count[tile], 1);
@@ -175,68 +217,140 @@ __device__ __forceinline__ void band_cta(const ParticleConst& c, const ParticleA
       else atomicOr(err, ERR_TILE_OVERFLOW);
     }
   }
-  const int ncell = bw * bw;
-  int2* table = P.band + (long long)p * bw * bw;
-  for (int base = 0; base < ncell; base += BAND_CTA * BAND_CHUNK) {
-    if (tid == 0) s_nq = 0;
-    __syncthreads();
-#pragma unroll 1
-    for (int j = 0; j < BAND_CHUNK; ++j) {
-      const int k = base + j * BAND_CTA + tid;
-      if (k >= ncell) break;
-      const int by = k / bw, bx = k - by * bw;
-      const int x = rc.xi - c.band_off + bx, y = rc.yi - c.band_off + by;
-      if (x < 0 || x >= c.nx || y < 0 || y >= c.ny) continue;
-      const int x0 = x - x % TILE_X, y0 = y - y % TILE_Y;
-      PartTile<float> q;
-      tile_geometry(rc, x0, y0, q);
-      if (quick_class(x - x0, y - y0, q) == CELL_BAND) s_queue[atomicAdd(&s_nq, 1)] = k;
+  // Lane r takes row r of the box and only the cells of that row that can be
+  // in the band: |x - X| between sqrt((R - 0.75)^2 - dy^2) and
+  // sqrt((R + 0.75)^2 - dy^2), widened by half a cell on either side (far
+  // more than the FP32 error of these bounds).  The quick test then decides
+  // each of these candidates exactly as the lattice kernel does.
+  const float cx = float(c.band_off) + rc.xfh, cy = float(c.band_off) + rc.yfh;  // centre in box coordinates
+  // the band lies between the inscribed and circumscribed circles' bounds
+  // of the quick test (an ellipse: semi-minor and semi-major axis; a disk: R)
+  const float ro = rc.r + 0.75f, ri = rc.near2 > 0.0f ? sqrtf(rc.near2) : 0.0f;
+  int nq = 0;
+  for (int by0 = 0; by0 < bw; by0 += 32) {
+    const int by = by0 + lane;
+    const int y = rc.yi - c.band_off + by;
+    int a0 = 0, a1 = -1, b0 = 0, b1 = -1;  // candidate runs [a0, a1], [b0, b1] of bx
+    if (by < bw && y >= 0 && y < c.ny) {
+      const float dy = (float(by) + 0.5f) - cy;
+      const float oa = ro * ro - dy * dy;
+      if (oa > -1.0f) {  // the row meets the widened outer circle
+        const float wa = sqrtf(fmaxf(oa, 0.0f)) + 0.5f;
+        const float ib = ri * ri - dy * dy;
+        const float wb = (ri > 0.0f && ib > 0.0f) ? sqrtf(ib) - 0.5f : 0.0f;
+        // cell bx is a candidate when |bx + 0.5 - cx| lies in [wb, wa]
+        a0 = max(0, (int)ceilf(cx - wa - 0.5f));
+        b1 = min(bw - 1, (int)floorf(cx + wa - 0.5f));
+        if (wb > 0.0f) {
+          a1 = (int)floorf(cx - wb - 0.5f);
+          b0 = (int)ceilf(cx + wb - 0.5f);
+        } else {  // one run through the middle
+          a1 = b1;
+          b0 = 0;
+          b1 = -1;
+        }
+        a1 = min(a1, bw - 1);
+        b0 = max(b0, 0);
+      }
     }
-    __syncthreads();
-    const int nq = s_nq;
-    for (int j = tid; j < nq; j += BAND_CTA) {
-      const int k = s_queue[j];
-      const int by = k / bw, bx = k - by * bw;
-      const int x = rc.xi - c.band_off + bx, y = rc.yi - c.band_off + by;
-      const int x0 = x - x % TILE_X, y0 = y - y % TILE_Y;
-      PartTile<float> q;
-      tile_geometry(rc, x0, y0, q);
-      float f;
-      const int cls = cell_fraction(x - x0, y - y0, q, f);
-      table[k] = make_int2(cls | (stamp << 2), __float_as_int(f));
+    const int na = max(a1 - a0 + 1, 0), nb = max(b1 - b0 + 1, 0);
+    int nmax = na + nb;
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+    for (int j = 0; j < nmax; ++j) {
+      bool in_band = false;
+      int k = 0;
+      if (j < na + nb) {
+        const int bx = j < na ? a0 + j : b0 + (j - na);
+        const int x = rc.xi - c.band_off + bx;
+        k = by * bw + bx;
+        if (x >= 0 && x < c.nx) {
+          const int x0 = x - x % TILE_X, y0 = y - y % TILE_Y;
+          PartTile<float> q;
+          tile_geometry(rc, x0, y0, q);
+          in_band = quick_class(x - x0, y - y0, q) == CELL_BAND;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, in_band);
+      if (in_band) queue[nq + __popc(m & ((1u << lane) - 1u))] = k;
+      nq += __popc(m);
+      if (nq > BAND_QUEUE - 32) {  // evaluate what is queued before it can overflow
+        __syncwarp();
+        band_evaluate<ELL>(c, P, p, stamp, rc, bw, queue, nq, lane);
+        __syncwarp();
+        nq = 0;
+      }
     }
-    __syncthreads();  // s_nq and the queue are reused by the next chunk
   }
+  __syncwarp();
+  band_evaluate<ELL>(c, P, p, stamp, rc, bw, queue, nq, lane);
 }
 
-// Advance of every particle, one thread each.
-__global__ void __launch_bounds__(128) particle_advance_kernel(const ParticleConst c, const ParticleArrays P,
-                                                               unsigned* err) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < c.np) advance_one(c, P, p, err);
+// The band pass of every disk (ELL false) or of every ellipse (ELL true),
+// one warp per particle; the particles of the other kind are left alone.
+template <bool ELL>
+__global__ void __launch_bounds__(32 * BAND_WARPS) particle_band_kernel(const ParticleConst c, const ParticleArrays P,
+                                                                        const TileLists TL, unsigned* err) {
+  __shared__ int s_queue[BAND_WARPS][BAND_QUEUE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * BAND_WARPS + warp;
+  if (p >= c.np || ((P.rb[p] != P.r[p]) != ELL)) return;  // the whole warp
+  band_one<ELL>(c, P, TL, err, p, c.band_stamp, s_queue[warp], lane);
 }
 
-// Lists and band table of every particle, one CTA each.
-__global__ void __launch_bounds__(BAND_CTA) particle_band_cta_kernel(const ParticleConst c, const ParticleArrays P,
-                                                                     const TileLists TL, unsigned* err) {
-  band_cta(c, P, TL, err, blockIdx.x, c.band_stamp);
+// One particle step (advance, then lists and band table) in one launch: the
+// two depend on the particle alone.  A CTA of STEP_WARPS warps takes
+// STEP_WARPS particles: warp 0 advances them, one lane each (so the FP64
+// instructions stay shared by many particles and the advance is spread over
+// the SMs), then each warp runs the band pass of one of them; the barrier
+// between makes the new records visible.  Ellipses get their band pass from
+// particle_band_kernel<true> after this kernel.
+constexpr int STEP_WARPS = 16;
+
+__global__ void __launch_bounds__(32 * STEP_WARPS, 1) particle_step_kernel(const ParticleConst c, const ParticleArrays P,
+                                                                        const TileLists TL, unsigned* err) {
+  __shared__ int s_queue[STEP_WARPS][BAND_QUEUE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p0 = blockIdx.x * STEP_WARPS;
+  if (warp == 0 && lane < STEP_WARPS && p0 + lane < c.np) advance_one(c, P, p0 + lane, err);
+  __syncthreads();
+  const int p = p0 + warp;
+  if (p >= c.np || P.rb[p] != P.r[p]) return;  // the whole warp
+  band_one<false>(c, P, TL, err, p, c.band_stamp, s_queue[warp], lane);
 }
 
 // The same over the particles of many cases, step k of a batch call.
-__global__ void __launch_bounds__(128) particle_advance_batch_kernel(const BatchParticles* __restrict__ cases,
-                                                                     const int2* __restrict__ items, int nitems) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nitems) return;
+__global__ void __launch_bounds__(32 * STEP_WARPS, 1)
+    particle_step_batch_kernel(const BatchParticles* __restrict__ cases, const int2* __restrict__ items, int nitems,
+                               int k) {
+  __shared__ int s_queue[STEP_WARPS][BAND_QUEUE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = blockIdx.x * STEP_WARPS;
+  if (warp == 0 && lane < STEP_WARPS && i0 + lane < nitems) {
+    const int2 it = items[i0 + lane];
+    const BatchParticles& d = cases[it.x];
+    advance_one(d.c, d.P, it.y, d.err);
+  }
+  __syncthreads();
+  const int i = i0 + warp;
+  if (i >= nitems) return;  // the whole warp
   const int2 it = items[i];
   const BatchParticles& d = cases[it.x];
-  advance_one(d.c, d.P, it.y, d.err);
-}
-__global__ void __launch_bounds__(BAND_CTA) particle_band_cta_batch_kernel(const BatchParticles* __restrict__ cases,
-                                                                           const int2* __restrict__ items, int k) {
-  const int2 it = items[blockIdx.x];
-  const BatchParticles& d = cases[it.x];
+  if (d.P.rb[it.y] != d.P.r[it.y]) return;
   const int nl = 1 - (d.tl ^ (k & 1));
-  band_cta(d.c, d.P, d.TL[nl], d.err, it.y, band_stamp_after(d.stamp, k + 1));
+  band_one<false>(d.c, d.P, d.TL[nl], d.err, it.y, band_stamp_after(d.stamp, k + 1), s_queue[warp], lane);
+}
+__global__ void __launch_bounds__(32 * BAND_WARPS)
+    particle_band_ellipse_batch_kernel(const BatchParticles* __restrict__ cases, const int2* __restrict__ items,
+                                       int nitems, int k) {
+  __shared__ int s_queue[BAND_WARPS][BAND_QUEUE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * BAND_WARPS + warp;
+  if (i >= nitems) return;  // the whole warp
+  const int2 it = items[i];
+  const BatchParticles& d = cases[it.x];
+  if (d.P.rb[it.y] == d.P.r[it.y]) return;
+  const int nl = 1 - (d.tl ^ (k & 1));
+  band_one<true>(d.c, d.P, d.TL[nl], d.err, it.y, band_stamp_after(d.stamp, k + 1), s_queue[warp], lane);
 }
 
 static inline dim3 pgrid(int n) { return dim3((unsigned)((n + 127) / 128)); }
@@ -250,23 +364,28 @@ cudaError_t launch_particle_range(const ParticleConst& c, const ParticleArrays& 
 cudaError_t launch_particle_band(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
                                  cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
-  particle_band_cta_kernel<<<(unsigned)c.np, BAND_CTA, 0, st>>>(c, P, TL, err);
+  const unsigned grid = (unsigned)((c.np + BAND_WARPS - 1) / BAND_WARPS);
+  particle_band_kernel<false><<<grid, 32 * BAND_WARPS, 0, st>>>(c, P, TL, err);
+  if (c.any_ellipse) particle_band_kernel<true><<<grid, 32 * BAND_WARPS, 0, st>>>(c, P, TL, err);
   return cudaGetLastError();
 }
-// The time step's particle part: the advance (thread per particle), then the
-// band pass (CTA per particle).
 cudaError_t launch_particle_step(const ParticleConst& c, const ParticleArrays& P, const TileLists& TL, unsigned* err,
                                  cudaStream_t st) {
   if (c.np == 0) return cudaSuccess;
-  particle_advance_kernel<<<pgrid(c.np), 128, 0, st>>>(c, P, err);
-  particle_band_cta_kernel<<<(unsigned)c.np, BAND_CTA, 0, st>>>(c, P, TL, err);
+  particle_step_kernel<<<(unsigned)((c.np + STEP_WARPS - 1) / STEP_WARPS), 32 * STEP_WARPS, 0, st>>>(c, P, TL, err);
+  if (c.any_ellipse)
+    particle_band_kernel<true><<<(unsigned)((c.np + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(c, P, TL,
+                                                                                                          err);
   return cudaGetLastError();
 }
 cudaError_t launch_particle_step_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
-                                       cudaStream_t st) {
+                                       bool any_ellipse, cudaStream_t st) {
   if (nitems == 0) return cudaSuccess;
-  particle_advance_batch_kernel<<<pgrid(nitems), 128, 0, st>>>(cases, items, nitems);
-  particle_band_cta_batch_kernel<<<(unsigned)nitems, BAND_CTA, 0, st>>>(cases, items, k);
+  particle_step_batch_kernel<<<(unsigned)((nitems + STEP_WARPS - 1) / STEP_WARPS), 32 * STEP_WARPS, 0, st>>>(
+      cases, items, nitems, k);
+  if (any_ellipse)
+    particle_band_ellipse_batch_kernel<<<(unsigned)((nitems + BAND_WARPS - 1) / BAND_WARPS), 32 * BAND_WARPS, 0, st>>>(
+        cases, items, nitems, k);
   return cudaGetLastError();
 }
 }  // namespace vlb

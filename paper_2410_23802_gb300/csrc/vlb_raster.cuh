@@ -52,10 +52,20 @@ __host__ __device__ __forceinline__ double add_rn(double a, double b) {
 
 enum : int { CELL_FLUID = 0, CELL_INTERFACE = 1, CELL_SOLID = 2 };
 
+// An ellipse as the FP64 lattice kernel sees it (the FP32 kernel reads
+// ellipses from their band tables and carries none of this).
+template <class C>
+struct EllPart {};
+template <>
+struct EllPart<double> {
+  int ell;                        // an ellipse
+  double ex, ey, ea, eb, ec, es;  // its centre, semi-axes, cos and sin of its angle
+};
+
 // One particle as seen from one tile (shared memory).  Coordinates are
 // relative to the tile's lower-left corner.
 template <class C>
-struct PartTile {
+struct PartTile : EllPart<C> {
   long long xq, yq, rq2;  // fixed-point centre and R^2 (2^-20 grid)
   C xh, xl, yh, yl;       // centre as an unevaluated sum hi + lo
   C r, far2, near2;       // radius, quick-reject bounds on the centre distance^2
@@ -184,6 +194,142 @@ __host__ __device__ __forceinline__ int quick_class(int il, int jl, const PartTi
   if (d2 >= p.far2) return CELL_FLUID;   // nearest point > R + 0.04
   if (d2 <= p.near2) return CELL_SOLID;  // farthest corner < R - 0.04
   return CELL_BAND;
+}
+
+// ---------------------------------------------------------------------------
+// Ellipses (reading R13), in FP64 with every product, sum and quotient
+// rounded one at a time, so that the class decisions are those of any other
+// FP64 evaluation in the same order (the oracle's among them).
+// ---------------------------------------------------------------------------
+struct EllFrame { double u, v; };
+// Point (px, py) in the ellipse's unit-disk frame: ((c dx + s dy) / a, (c dy - s dx) / b).
+__host__ __device__ __forceinline__ EllFrame ellipse_frame(double px, double py, double X, double Y, double a,
+                                                           double b, double c, double s) {
+  const double dx = add_rn(px, -X), dy = add_rn(py, -Y);
+  EllFrame f;
+#ifdef __CUDA_ARCH__
+  f.u = __ddiv_rn(add_rn(mul_rn(c, dx), mul_rn(s, dy)), a);
+  f.v = __ddiv_rn(add_rn(mul_rn(c, dy), -mul_rn(s, dx)), b);
+#else
+  f.u = (c * dx + s * dy) / a;
+  f.v = (c * dy - s * dx) / b;
+#endif
+  return f;
+}
+__host__ __device__ __forceinline__ double quad_uv(double u, double v) { return add_rn(mul_rn(u, u), mul_rn(v, v)); }
+
+// Class of cell [i, i+1] x [j, j+1]: SOLID when its four corners lie in the
+// closed ellipse, FLUID when the least value of the quadratic form over the
+// cell (each edge's convex quadratic at its clamped vertex) is >= 1.
+__host__ __device__ __forceinline__ int ellipse_cell_class(int i, int j, double X, double Y, double a, double b,
+                                                           double c, double s) {
+  double cu[4], cv[4];
+  const double xs[4] = {double(i), double(i + 1), double(i + 1), double(i)};
+  const double ys[4] = {double(j), double(j), double(j + 1), double(j + 1)};
+  double qmax = 0.0, qmin = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    const EllFrame f = ellipse_frame(xs[k], ys[k], X, Y, a, b, c, s);
+    cu[k] = f.u; cv[k] = f.v;
+    const double q = quad_uv(f.u, f.v);
+    qmax = k == 0 ? q : (q > qmax ? q : qmax);
+    qmin = k == 0 ? q : (q < qmin ? q : qmin);
+  }
+  if (qmax <= 1.0) return CELL_SOLID;
+  if (double(i) <= X && X <= double(i + 1) && double(j) <= Y && Y <= double(j + 1)) return CELL_INTERFACE;
+  for (int k = 0; k < 4; ++k) {
+    const int k1 = (k + 1) & 3;
+    const double du = add_rn(cu[k1], -cu[k]), dv = add_rn(cv[k1], -cv[k]);
+    const double A = quad_uv(du, dv);
+#ifdef __CUDA_ARCH__
+    double t = __ddiv_rn(-add_rn(mul_rn(cu[k], du), mul_rn(cv[k], dv)), A);
+#else
+    double t = -(cu[k] * du + cv[k] * dv) / A;
+#endif
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    const double q = quad_uv(add_rn(cu[k], mul_rn(t, du)), add_rn(cv[k], mul_rn(t, dv)));
+    qmin = q < qmin ? q : qmin;
+  }
+  return qmin >= 1.0 ? CELL_FLUID : CELL_INTERFACE;
+}
+
+// Area of the unit disk within the convex quadrilateral (us, vs) (counter-
+// clockwise), by Green's theorem on the intersection's boundary: inside
+// parts of the edges contribute (u_a v_b - u_b v_a) / 2, the arcs between
+// leaving the disk on one edge and entering it on a later one half their
+// counter-clockwise angle; a vertex on the circle (exit and entry at the same
+// point of consecutive edges) adds no arc.
+__host__ __device__ __forceinline__ double quad_unit_disk_area(const double (&us)[4], const double (&vs)[4]) {
+  double pa_u[4], pa_v[4], pb_u[4], pb_v[4];
+  int edge[4];
+  int m = 0;
+  for (int k = 0; k < 4; ++k) {
+    const int k1 = (k + 1) & 3;
+    const double u0 = us[k], v0 = vs[k];
+    const double du = us[k1] - u0, dv = vs[k1] - v0;
+    const double A = du * du + dv * dv, B = u0 * du + v0 * dv, C = u0 * u0 + v0 * v0 - 1.0;
+    const double disc = B * B - A * C;
+    if (A == 0.0 || disc <= 0.0) continue;
+    const double r = sqrt(disc);
+    double t0 = (-B - r) / A, t1 = (-B + r) / A;
+    t0 = t0 > 0.0 ? t0 : 0.0;
+    t1 = t1 < 1.0 ? t1 : 1.0;
+    if (t1 <= t0) continue;
+    pa_u[m] = u0 + t0 * du; pa_v[m] = v0 + t0 * dv;
+    pb_u[m] = u0 + t1 * du; pb_v[m] = v0 + t1 * dv;
+    edge[m] = k;
+    ++m;
+  }
+  if (m == 0) {
+    bool inside = true;  // the disk's centre inside the polygon (then the whole disk is)
+    for (int k = 0; k < 4; ++k) {
+      const int k1 = (k + 1) & 3;
+      inside = inside && ((us[k1] - us[k]) * (0.0 - vs[k]) - (vs[k1] - vs[k]) * (0.0 - us[k]) >= 0.0);
+    }
+    return inside ? 3.14159265358979323846 : 0.0;
+  }
+  double area = 0.0;
+  for (int q = 0; q < m; ++q) {
+    area += 0.5 * (pa_u[q] * pb_v[q] - pb_u[q] * pa_v[q]);
+    const int n1 = q + 1 < m ? q + 1 : 0;
+    const double qu = pa_u[n1], qv = pa_v[n1];
+    const double gu = qu - pb_u[q], gv = qv - pb_v[q];
+    if (edge[n1] == ((edge[q] + 1) & 3) && gu * gu + gv * gv < 1e-24) continue;
+    double ang = atan2(pb_u[q] * qv - pb_v[q] * qu, pb_u[q] * qu + pb_v[q] * qv);
+    if (ang < 0.0) ang += 2.0 * 3.14159265358979323846;
+    area += 0.5 * ang;
+  }
+  return area;
+}
+
+// Exact area of the ellipse in cell [i, i+1] x [j, j+1] (the cell is a
+// parallelogram in the unit-disk frame; areas scale by a b).
+__host__ __device__ __forceinline__ double ellipse_cell_area(int i, int j, double X, double Y, double a, double b,
+                                                             double c, double s) {
+  const double xs[4] = {double(i), double(i + 1), double(i + 1), double(i)};
+  const double ys[4] = {double(j), double(j), double(j + 1), double(j + 1)};
+  double us[4], vs[4];
+  for (int k = 0; k < 4; ++k) {
+    const EllFrame f = ellipse_frame(xs[k], ys[k], X, Y, a, b, c, s);
+    us[k] = f.u; vs[k] = f.v;
+  }
+  return a * b * quad_unit_disk_area(us, vs);
+}
+
+// Class and fraction of cell (gi, gj) of the lattice for an ellipse; the
+// quick test on the circumscribed and inscribed circles first (its SOLID and
+// FLUID answers are exact), the FP64 class and area for the band cells.
+template <class C>
+__host__ __device__ __forceinline__ int ellipse_cell_fraction(int il, int jl, int gi, int gj, const PartTile<C>& p,
+                                                              C& fsp) {
+  const int qc = quick_class(il, jl, p);
+  if (qc == CELL_FLUID) { fsp = C(0); return CELL_FLUID; }
+  if (qc == CELL_SOLID) { fsp = C(1); return CELL_SOLID; }
+  const int cls = ellipse_cell_class(gi, gj, p.ex, p.ey, p.ea, p.eb, p.ec, p.es);
+  if (cls == CELL_SOLID) { fsp = C(1); return cls; }
+  if (cls == CELL_FLUID) { fsp = C(0); return cls; }
+  const double ar = ellipse_cell_area(gi, gj, p.ex, p.ey, p.ea, p.eb, p.ec, p.es);
+  fsp = C(ar < 0.0 ? 0.0 : (ar > 1.0 ? 1.0 : ar));
+  return cls;
 }
 
 // Class and solid fraction of tile cell (il, jl) for one particle.

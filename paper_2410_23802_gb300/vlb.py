@@ -36,7 +36,7 @@ class vlb_params(ctypes.Structure):
         ("thermal_rates_mode", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("max_particles", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("outflow_mask", ctypes.c_int32), ("reserved1", ctypes.c_int32),
         ("tau_f", ctypes.c_double),
         ("lambda_q_flow", ctypes.c_double),
         ("s_e", ctypes.c_double),
@@ -83,6 +83,7 @@ def _load():
         "vlb_set_stream": (ctypes.c_int, [h, ctypes.c_void_p]),
         "vlb_set_fixed_temperature": (ctypes.c_int, [h, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
         "vlb_add_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
+        "vlb_add_ellipses": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d, d, d]),
         "vlb_step": (ctypes.c_int, [h, ctypes.c_int32]),
         "vlb_insert_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
         "vlb_step_batch": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
@@ -141,10 +142,16 @@ def _check(status: int, h=None):
 
 
 def vlb_params_default(**overrides) -> vlb_params:
+    """The library's defaults with overrides by field name; ``outflow`` (four
+    flags, sides x-, x+, y-, y+) sets ``outflow_mask``."""
     p = vlb_params()
     _check(_lib.vlb_params_default(ctypes.byref(p)))
     for k, v in overrides.items():
-        if k in ("periodic", "thermal_wall", "wall_T", "gravity"):
+        if k == "outflow":
+            p.outflow_mask = sum(1 << i for i, flag in enumerate(v) if flag)
+        elif not hasattr(p, k):
+            raise AttributeError(f"vlb_params has no field {k}")
+        elif k in ("periodic", "thermal_wall", "wall_T", "gravity"):
             arr = getattr(p, k)
             for i, x in enumerate(v):
                 arr[i] = x
@@ -171,6 +178,19 @@ def vlb_add_particles(h, xy, radius, T0, k_ratio=None, uv=None, omega=None):
     conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)  # noqa: E731
     k_ratio, uv, omega = conv(k_ratio), conv(uv), conv(omega)
     _check(_lib.vlb_add_particles(h, n, _ptr(xy), _ptr(radius), _ptr(T0), _ptr(k_ratio), _ptr(uv), _ptr(omega)), h)
+
+
+def vlb_add_ellipses(h, xy, semi_a, semi_b, theta, T0, k_ratio=None, uv=None, omega=None):
+    xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+    semi_a = np.ascontiguousarray(semi_a, dtype=np.float64)
+    semi_b = np.ascontiguousarray(semi_b, dtype=np.float64)
+    theta = np.ascontiguousarray(theta, dtype=np.float64)
+    T0 = np.ascontiguousarray(T0, dtype=np.float64)
+    n = semi_a.shape[0]
+    conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)  # noqa: E731
+    k_ratio, uv, omega = conv(k_ratio), conv(uv), conv(omega)
+    _check(_lib.vlb_add_ellipses(h, n, _ptr(xy), _ptr(semi_a), _ptr(semi_b), _ptr(theta), _ptr(T0), _ptr(k_ratio),
+                                 _ptr(uv), _ptr(omega)), h)
 
 
 def vlb_insert_particles(h, xy, radius, T0, k_ratio=None, uv=None, omega=None):
@@ -356,6 +376,9 @@ class Lattice:
 
     def add_particles(self, *a, **k):
         vlb_add_particles(self.h, *a, **k)
+
+    def add_ellipses(self, *a, **k):
+        vlb_add_ellipses(self.h, *a, **k)
 
     def step(self, n: int = 1):
         vlb_step(self.h, n)

@@ -55,6 +55,8 @@ class Case:
     T0: list
     k_ratio: list | None = None
     fixed_T: list | None = None   # particles held at their temperature T0
+    semi_minor: list | None = None  # ellipses: semi-minor axes (radius = semi-major axis)
+    theta0: list | None = None      # ellipses: initial angle of the major axis
 
     @property
     def cells(self) -> int:
@@ -131,6 +133,34 @@ def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision
                   thermal_rates_mode=0, precision=precision)
     return Case(f"fixed-temperature sedimentation {nx}x{ny}, Gr={gr:g}", params, [1.5 * D], [ny - 10.0 * D],
                 [D / 2.0], [0.0], None, [1])
+
+
+def ellipse_sedimentation(length_w: float = 30.0, theta0: float = math.pi / 4, x_offset: float = 0.0,
+                          precision: str = "fp32") -> Case:
+    """Isothermal sedimentation of an elliptical particle in a long channel
+    (Sec. 3.2): channel width L = 104 cells (dx = 1/260 cm for L = 0.4 cm),
+    semi-axes a = 13 and b = 6.5 cells (0.05 and 0.025 cm), rho_s/rho_f = 1.1,
+    nu = 0.01 cm^2/s, |g| = 980 cm/s^2, tau_f = 0.6 (so dt = nu_lu dx^2 / nu
+    and g = 980 dt^2 / dx in lattice units); the particle starts at rest in
+    the middle of the channel, 3 L below its top, its major axis at theta0 to
+    the horizontal (x_offset moves it sideways); no-slip side walls and top,
+    the bottom open (fully developed outflow); only the flow matters (beta =
+    0, uniform temperature).  The channel is length_w widths long (30 in the
+    paper)."""
+    W = 104
+    dx = 0.4 / W                       # cm
+    nu_lu = (0.6 - 0.5) / 3.0
+    dt = nu_lu * dx * dx / 0.01        # s
+    g = 980.0 * dt * dt / dx           # lattice units
+    ny = int(round(length_w * W))
+    params = dict(nx=W, ny=ny, tau_f=0.6, prandtl=0.7, rho_ratio=1.1, cv_ratio=1.0, k_ratio_default=1.0,
+                  gravity=(0.0, -g), beta=0.0, T_ref=1.0, T_fluid_init=1.0, thermal_wall=(0, 0, 0, 0),
+                  wall_T=(0.0, 0.0, 0.0, 0.0), thermal_rates_mode=0, outflow=(0, 0, 1, 0), precision=precision)
+    c = Case(f"elliptical particle in a {W}x{ny} channel (a=13, b=6.5, theta0={theta0:.4f})", params,
+             [W / 2.0 + x_offset], [ny - 3.0 * W], [13.0], [1.0])
+    c.semi_minor = [6.5]
+    c.theta0 = [theta0]
+    return c
 
 
 def conjugate_sedimentation(r_cv: float, length_d: float = 40.0, precision: str = "fp32") -> Case:

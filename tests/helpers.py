@@ -13,7 +13,10 @@ def gpu_lattice(case, precision=None, max_particles=None, **over):
     n = len(case.x)
     p = V.vlb_params_default(precision=prec, max_particles=max_particles or max(n, 1), **prm)
     lat = V.Lattice(p)
-    if n:
+    if n and getattr(case, "semi_minor", None) is not None:
+        lat.add_ellipses(np.column_stack([case.x, case.y]), case.radius, case.semi_minor, case.theta0, case.T0,
+                         k_ratio=case.k_ratio)
+    elif n:
         xy = np.column_stack([case.x, case.y])
         lat.add_particles(xy, case.radius, case.T0, k_ratio=case.k_ratio)
         if getattr(case, "fixed_T", None) is not None:
@@ -25,10 +28,12 @@ def oracle_sim(case, **over):
     from oracle import vlbref as O
     prm = {k: v for k, v in case.params.items() if k != "precision"}
     prm.update(over)
-    if "periodic" in prm:
-        prm["periodic"] = tuple(bool(v) for v in prm["periodic"])
+    for key in ("periodic", "outflow"):
+        if key in prm:
+            prm[key] = tuple(bool(v) for v in prm[key])
     return O.Simulation(O.Params(**prm), case.x, case.y, case.radius, case.T0, k_ratio=case.k_ratio,
-                        fixed_T=getattr(case, "fixed_T", None))
+                        fixed_T=getattr(case, "fixed_T", None), semi_minor=getattr(case, "semi_minor", None),
+                        theta=getattr(case, "theta0", None))
 
 
 def rel_l2(a, b):

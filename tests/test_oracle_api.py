@@ -8,7 +8,7 @@ import re
 import numpy as np
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CORE = ["create", "add_particles", "insert_particles", "set_fixed_temperature", "step", "get_fields", "get_particle_count",
+CORE = ["create", "add_particles", "add_ellipses", "insert_particles", "set_fixed_temperature", "step", "get_fields", "get_particle_count",
         "get_particle_state", "get_audit", "get_step", "last_error", "destroy"]
 
 
@@ -23,7 +23,7 @@ def test_every_core_entry_point_has_an_oracle_twin():
     for name in CORE:
         assert callable(getattr(O, "vlbref_" + name)), name
     # inputs in the header's order (the C out-parameters of scalars are returned instead)
-    for name in ("add_particles", "insert_particles", "set_fixed_temperature", "step", "get_fields",
+    for name in ("add_particles", "add_ellipses", "insert_particles", "set_fixed_temperature", "step", "get_fields",
                  "get_particle_state"):
         py = list(inspect.signature(getattr(O, "vlbref_" + name)).parameters)
         assert py == _header_params(name), name
