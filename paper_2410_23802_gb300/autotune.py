@@ -1,10 +1,8 @@
 """Autotuner of the lattice kernel's build-time shape.
 
 The tile height (VLB_TILE_Y: CTAs of 32 x TILE_Y threads, one per tile of as
-many cells), the bound on resident CTAs per SM that sets the register
-budget (VLB_LATTICE_MIN_BLOCKS) and the L2 prefetch distance of the step
-kernel in occupancy waves (VLB_PREFETCH_WAVES) are compile-time constants of
-the kernels.
+many cells) and the bound on resident CTAs per SM that sets the register
+budget (VLB_LATTICE_MIN_BLOCKS) are compile-time constants of the kernels.
 The tuner builds the library once per candidate shape (each into a file of
 its own), times a workload with each build in a fresh process on the GPU,
 and records every result and the fastest shape in tuned.json, which
@@ -27,24 +25,22 @@ import sys
 
 from . import build as B
 
-# (tile height, CTAs per SM the registers are budgeted for (None: 1024
-# threads per SM), L2 prefetch distance in occupancy waves (0: none))
-CANDIDATES = [(4, None, 1), (4, None, 0), (4, None, 2), (2, None, 1), (8, None, 1), (4, 6, 1)]
+# (tile height, CTAs per SM the registers are budgeted for; None: 1024 threads per SM)
+CANDIDATES = [(4, None), (2, None), (8, None), (4, 6)]
 
 
-def candidate_defines(tile_y: int, min_blocks: int | None, waves: int = 1) -> list[str]:
+def candidate_defines(tile_y: int, min_blocks: int | None) -> list[str]:
     d = [f"VLB_TILE_Y={tile_y}"]
     if min_blocks is not None:
         d.append(f"VLB_LATTICE_MIN_BLOCKS={min_blocks}")
-    d.append(f"VLB_PREFETCH_WAVES={waves}")
     return d
 
 
-_SHORT = {"VLB_TILE_Y": "y", "VLB_LATTICE_MIN_BLOCKS": "b", "VLB_PREFETCH_WAVES": "w"}
+_SHORT = {"VLB_TILE_Y": "y", "VLB_LATTICE_MIN_BLOCKS": "b"}
 
 
 def candidate_tag(defines: list[str]) -> str:
-    """File name of a candidate build, e.g. tune_y4_w1 or tune_y4_b6_w1."""
+    """File name of a candidate build, e.g. tune_y4 or tune_y4_b6."""
     return "tune_" + "_".join(_SHORT[x.split("=")[0]] + x.split("=")[1] for x in defines)
 
 
@@ -99,8 +95,8 @@ def tune(workload: str, steps: int = 200, path: str = B.TUNED, use: bool = True,
     build = build or (lambda defines, out: B.build(defines=defines, out=out))
     timer = timer or time_candidate
     results = []
-    for tile_y, mb, waves in CANDIDATES:
-        defines = candidate_defines(tile_y, mb, waves)
+    for tile_y, mb in CANDIDATES:
+        defines = candidate_defines(tile_y, mb)
         lib = os.path.join(B.BUILD, candidate_tag(defines) + ".so")
         build(defines, lib)
         r = timer(lib, workload, steps)

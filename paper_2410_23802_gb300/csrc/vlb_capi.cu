@@ -23,6 +23,7 @@
 
 #include "../../include/vlb.h"
 #include "vlb_common.cuh"
+#include "vlb_internal.h"
 #include "vlb_kernels.h"
 
 using namespace vlb;
@@ -33,6 +34,7 @@ struct vlb_handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int device = 0;  // the device current at vlb_create, which holds every buffer
+  cudaMemPool_t pool = nullptr;  // when set (served cases), buffers come from this stream-ordered pool
   int nx = 0, ny = 0, pitch = 0, ntx = 0, nty = 0;
   long long plane = 0;
   size_t ssize = 0;          // bytes per stored population
@@ -57,6 +59,7 @@ struct vlb_handle {
   size_t pbytes = 0;  // bytes of the particle block at pbase
   // device error word and its pinned host copy (refreshed in stream order)
   unsigned* err_host = nullptr;
+  bool err_host_external = false;  // the served mode's arena owns it
   unsigned* err_dev = nullptr;
   double* audit_scratch = nullptr;
   double* audit_out = nullptr;
@@ -84,6 +87,19 @@ struct vlb_handle {
 };
 
 static thread_local std::string g_create_error;
+
+// Device buffers of a handle: cudaMalloc, or for a handle made in a memory
+// pool (the served mode's) stream-ordered allocation from it, whose frees do
+// not synchronise the device.
+static cudaError_t dev_alloc(vlb_handle* h, void** p, size_t bytes) {
+  if (h->pool) return cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream);
+  return cudaMalloc(p, bytes);
+}
+static void dev_free(vlb_handle* h, void* p) {
+  if (!p) return;
+  if (h->pool) cudaFreeAsync(p, h->stream);
+  else cudaFree(p);
+}
 
 static vlb_status fail(vlb_handle* h, vlb_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -184,31 +200,26 @@ static void fill_const(vlb_handle* h, LatticeConst<C>& K) {
   K.se_f = C(p.thermal_rates_mode == 0 ? 1.0 / (0.5 + 0.25 / (tgf - 0.5)) : 1.0);
   K.k3_cref = C(3.0 / cref);
   K.gk_f = C(-3.0 / (cref * tgf));
-  // L2 prefetch distance: whole occupancy waves of the step kernel
-  int sms = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) sms = 0;
-  const int per_sm = lattice_step_ctas_per_sm(p.precision == VLB_FP64, h->storage);
-  K.pf_tiles = sms * per_sm * lattice_prefetch_waves();
 }
 
 extern "C" {
 
 static void free_all(vlb_handle* h) {
   for (int b = 0; b < 2; ++b) {
-    if (h->pop[b]) cudaFree(h->pop[b]);
-    if (h->spl[b]) cudaFree(h->spl[b]);
+    dev_free(h, h->pop[b]);
+    dev_free(h, h->spl[b]);
   }
-  if (h->macro) cudaFree(h->macro);
-  if (h->pbase) cudaFree(h->pbase);
+  dev_free(h, h->macro);
+  dev_free(h, h->pbase);
   for (int b = 0; b < 2; ++b) {
-    if (h->TL[b].count) cudaFree(h->TL[b].count);
-    if (h->TL[b].ids) cudaFree(h->TL[b].ids);
+    dev_free(h, h->TL[b].count);
+    dev_free(h, h->TL[b].ids);
   }
-  if (h->P.mes) cudaFree(h->P.mes);
-  if (h->P.band) cudaFree(h->P.band);
-  if (h->audit_scratch) cudaFree(h->audit_scratch);
-  if (h->err_host) cudaFreeHost(h->err_host);
-  if (h->err_dev) cudaFree(h->err_dev);
+  dev_free(h, h->P.mes);
+  dev_free(h, h->P.band);
+  dev_free(h, h->audit_scratch);
+  if (h->err_host && !h->err_host_external) cudaFreeHost(h->err_host);
+  dev_free(h, h->err_dev);
   for (auto& e : h->ev) cudaEventDestroy(e);
   if (h->join) cudaEventDestroy(h->join);
   if (h->pstage) cudaFreeHost(h->pstage);
@@ -309,7 +320,11 @@ vlb_status vlb_device_bytes(const vlb_params* pp, int32_t n, const double* radiu
   return VLB_OK;
 }
 
-vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
+vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) { return vlb_create_in(pp, nullptr, out); }
+
+}  // extern "C"
+
+vlb_status vlb_create_in(const vlb_params* pp, const vlb_handle_alloc* alloc, vlb_handle** out) {
   if (!out) return fail(nullptr, VLB_EINVAL, "out is NULL");
   *out = nullptr;
   if (!pp) return fail(nullptr, VLB_EINVAL, "params is NULL");
@@ -319,6 +334,11 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   vlb_handle* h = new (std::nothrow) vlb_handle();
   if (!h) return fail(nullptr, VLB_ENOMEM, "host allocation");
   h->p = p;
+  if (alloc) {
+    h->pool = alloc->pool;
+    h->err_host = alloc->err_host;
+    h->err_host_external = alloc->err_host != nullptr;
+  }
   h->nx = p.nx;
   h->ny = p.ny;
   const Layout L = layout_of(p);
@@ -346,21 +366,21 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   h->own_stream = true;
   const size_t popbytes = (size_t)18 * h->plane * h->ssize;
   for (int b = 0; b < 2; ++b) {
-    if ((e = cudaMalloc(&h->pop[b], popbytes)) != cudaSuccess) return bail(e, "populations");
-    if ((e = cudaMalloc(&h->spl[b], (size_t)h->plane * h->esize)) != cudaSuccess) return bail(e, "S plane");
+    if ((e = dev_alloc(h, &h->pop[b], popbytes)) != cudaSuccess) return bail(e, "populations");
+    if ((e = dev_alloc(h, &h->spl[b], (size_t)h->plane * h->esize)) != cudaSuccess) return bail(e, "S plane");
     cudaMemsetAsync(h->spl[b], 0, (size_t)h->plane * h->esize, h->stream);
   }
-  if ((e = cudaMalloc(&h->macro, (size_t)7 * h->plane * h->esize)) != cudaSuccess) return bail(e, "macros");
+  if ((e = dev_alloc(h, &h->macro, (size_t)7 * h->plane * h->esize)) != cudaSuccess) return bail(e, "macros");
   const long long ntiles = (long long)h->ntx * h->nty;
   for (int b = 0; b < 2; ++b) {
-    if ((e = cudaMalloc(&h->TL[b].count, ntiles * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
-    if ((e = cudaMalloc(&h->TL[b].ids, ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
+    if ((e = dev_alloc(h, reinterpret_cast<void**>(&h->TL[b].count), ntiles * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
+    if ((e = dev_alloc(h, reinterpret_cast<void**>(&h->TL[b].ids), ntiles * TILE_CAP * sizeof(int))) != cudaSuccess) return bail(e, "tiles");
     cudaMemsetAsync(h->TL[b].count, 0, ntiles * sizeof(int), h->stream);
   }
   // particle arrays (int4 and record loads need 16-byte alignment)
   const size_t capn = (size_t)std::max(h->cap, 1);
   const size_t pbytes = particle_block_bytes(capn);
-  if ((e = cudaMalloc(&h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
+  if ((e = dev_alloc(h, &h->pbase, pbytes)) != cudaSuccess) return bail(e, "particles");
   h->pbytes = pbytes;
   {
     char* b = static_cast<char*>(h->pbase);
@@ -377,18 +397,20 @@ vlb_status vlb_create(const vlb_params* pp, vlb_handle** out) {
   }
   cudaMemsetAsync(h->pbase, 0, pbytes, h->stream);
   h->audit_blocks = AUDIT_BLOCKS;
-  if ((e = cudaMalloc(&h->audit_scratch, (3 * h->audit_blocks + 3) * sizeof(double))) != cudaSuccess)
+  if ((e = dev_alloc(h, reinterpret_cast<void**>(&h->audit_scratch), (3 * h->audit_blocks + 3) * sizeof(double))) != cudaSuccess)
     return bail(e, "audit");
   h->audit_out = h->audit_scratch + 3 * h->audit_blocks;
-  if ((e = cudaHostAlloc(&h->err_host, sizeof(unsigned), cudaHostAllocDefault)) != cudaSuccess)
+  if (!h->err_host_external && (e = cudaHostAlloc(&h->err_host, sizeof(unsigned), cudaHostAllocDefault)) != cudaSuccess)
     return bail(e, "error word");
   *h->err_host = 0;
-  if ((e = cudaMalloc(&h->err_dev, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
+  if ((e = dev_alloc(h, reinterpret_cast<void**>(&h->err_dev), sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
   cudaMemsetAsync(h->err_dev, 0, sizeof(unsigned), h->stream);
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(e, "create sync");
   *out = h;
   return VLB_OK;
 }
+
+extern "C" {
 
 vlb_status vlb_set_fixed_temperature(vlb_handle* h, int32_t first, int32_t n, const int32_t* held) {
   if (!h) return VLB_EINVAL;
@@ -576,10 +598,10 @@ static vlb_status initialize(vlb_handle* h) {
     // exchange accumulators and band tables for max_particles disks (later
     // insertions append to them): zero before the first lattice pass
     const size_t capn = (size_t)h->cap;
-    CK(h, cudaMalloc(&h->P.mes, capn * 6 * sizeof(unsigned long long)));
+    CK(h, dev_alloc(h, reinterpret_cast<void**>(&h->P.mes), capn * 6 * sizeof(unsigned long long)));
     CK(h, cudaMemsetAsync(h->P.mes, 0, capn * 6 * sizeof(unsigned long long), h->stream));
     const size_t bw = 2 * (size_t)band_off + 1;
-    CK(h, cudaMalloc(&h->P.band, capn * bw * bw * sizeof(int2)));
+    CK(h, dev_alloc(h, reinterpret_cast<void**>(&h->P.band), capn * bw * bw * sizeof(int2)));
     CK(h, cudaMemsetAsync(h->P.band, 0, capn * bw * bw * sizeof(int2), h->stream));
   }
   if (n > 0) {
@@ -758,7 +780,12 @@ void fill_lattice_desc(vlb_handle* h, const LatticeConst<C>& K, int tile0, Batch
 
 extern "C" {
 
-vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed) {
+}  // extern "C"
+
+// The batched step; the descriptor staging block and its event are the
+// caller's when given (stage != nullptr), else those of the leading handle.
+static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed,
+                                  unsigned char** stage, size_t* stage_cap, cudaEvent_t* stage_copied) {
   if (failed) *failed = -1;
   if (n < 0 || (n > 0 && !hs)) return fail(nullptr, VLB_EINVAL, "vlb_step_batch: n < 0 or no handle array");
   if (nsteps < 0) return fail(nullptr, VLB_EINVAL, "vlb_step_batch: nsteps < 0");
@@ -826,18 +853,24 @@ vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int3
     g.table_off = bytes;
     bytes = align16(bytes + sizeof(int) * nt);
   }
-  // the staging block of the previous call led by hs[0] is free once its copy ran
+  // the staging block of the previous call (led by hs[0], or the caller's)
+  // is free once its copy ran
   vlb_handle* h0 = hs[0];
-  if (!h0->bcopied) BCK(0, cudaEventCreateWithFlags(&h0->bcopied, cudaEventDisableTiming));
-  BCK(0, cudaEventSynchronize(h0->bcopied));
-  if (h0->bhost_cap < bytes) {
-    if (h0->bhost) cudaFreeHost(h0->bhost);
-    h0->bhost = nullptr;
-    h0->bhost_cap = 0;
-    BCK(0, cudaMallocHost(reinterpret_cast<void**>(&h0->bhost), bytes));
-    h0->bhost_cap = bytes;
+  if (!stage) {
+    stage = &h0->bhost;
+    stage_cap = &h0->bhost_cap;
+    stage_copied = &h0->bcopied;
   }
-  unsigned char* hostp = h0->bhost;
+  if (!*stage_copied) BCK(0, cudaEventCreateWithFlags(stage_copied, cudaEventDisableTiming));
+  BCK(0, cudaEventSynchronize(*stage_copied));
+  if (*stage_cap < bytes) {
+    if (*stage) cudaFreeHost(*stage);
+    *stage = nullptr;
+    *stage_cap = 0;
+    BCK(0, cudaMallocHost(reinterpret_cast<void**>(stage), bytes));
+    *stage_cap = bytes;
+  }
+  unsigned char* hostp = *stage;
   std::memset(hostp, 0, bytes);
   auto* bp = reinterpret_cast<BatchParticles*>(hostp);
   for (int i = 0; i < n; ++i) {
@@ -877,7 +910,7 @@ vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int3
   unsigned char* dev = nullptr;
   BCK(0, cudaMallocAsync(reinterpret_cast<void**>(&dev), bytes, bs));
   cudaError_t e = cudaMemcpyAsync(dev, hostp, bytes, cudaMemcpyHostToDevice, bs);
-  if (e == cudaSuccess) e = cudaEventRecord(h0->bcopied, bs);
+  if (e == cudaSuccess) e = cudaEventRecord(*stage_copied, bs);
   const auto* d_part = reinterpret_cast<const BatchParticles*>(dev);
   const auto* d_items = reinterpret_cast<const int2*>(dev + items_off);
   const int nitems = (int)items.size();
@@ -915,6 +948,17 @@ vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int3
   }
   return VLB_OK;
 #undef BCK
+}
+
+vlb_status vlb_step_batch_staged(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed,
+                                 unsigned char** stage, size_t* stage_cap, cudaEvent_t* stage_copied) {
+  return step_batch_impl(hs, n, nsteps, failed, stage, stage_cap, stage_copied);
+}
+
+extern "C" {
+
+vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed) {
+  return step_batch_impl(hs, n, nsteps, failed, nullptr, nullptr, nullptr);
 }
 
 vlb_status vlb_synchronize(vlb_handle* h) {
@@ -966,6 +1010,39 @@ vlb_status vlb_get_fields(vlb_handle* h, uint32_t mask, double* rho, double* ux,
   }
   return VLB_OK;
 }
+
+}  // extern "C"
+
+size_t vlb_value_bytes(const vlb_handle* h) { return h->esize; }
+
+vlb_status vlb_check_flags(vlb_handle* h) { return h ? device_flags(h) : VLB_EINVAL; }
+
+vlb_status vlb_readback_async(vlb_handle* h, void* fields, double* pstate, cudaEvent_t ev) {
+  if (!h || !fields || !ev) return VLB_EINVAL;
+  vlb_status s = device_flags(h);
+  if (s != VLB_OK) return s;
+  if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
+  if (!h->macros_valid) {
+    if ((s = launch_lattice(h, MODE_MACROS, 1 - h->cur, h->cur, h->tl)) != VLB_OK) return s;
+    h->macros_valid = true;
+  }
+  const size_t row = (size_t)h->nx * h->esize;
+  for (int k = 0; k < 5; ++k) {
+    const char* src = static_cast<const char*>(h->macro) + (size_t)k * h->plane * h->esize;
+    char* dst = static_cast<char*>(fields) + (size_t)k * h->ny * row;
+    CK(h, cudaMemcpy2DAsync(dst, row, src, h->pitch * h->esize, row, h->ny, cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (h->np > 0 && pstate) {
+    const size_t cap = (size_t)std::max(h->cap, 1);
+    CK(h, cudaMemcpy2DAsync(pstate, h->np * sizeof(double), h->P.x, a256(cap * sizeof(double)), h->np * sizeof(double),
+                            12, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(h, pull_flags(h));
+  CK(h, cudaEventRecord(ev, h->stream));
+  return VLB_OK;
+}
+
+extern "C" {
 
 vlb_status vlb_get_particle_count(vlb_handle* h, int32_t* n) {
   if (!h || !n) return VLB_EINVAL;
@@ -1309,7 +1386,9 @@ vlb_status vlb_profile_end(vlb_handle* h, double* lattice_ms, int32_t* lattice_l
 
 void vlb_destroy(vlb_handle* h) {
   if (!h) return;
-  if (h->stream) cudaStreamSynchronize(h->stream);
+  // a handle in a memory pool (served mode) frees in stream order: the
+  // stream, which other handles share, is not waited for
+  if (h->stream && !h->pool) cudaStreamSynchronize(h->stream);
   free_all(h);
   delete h;
 }

@@ -156,7 +156,6 @@ struct LatticeConst {
   int band_off;            // half-width of the band tables (cells)
   int band_stamp;          // level stamp the band tables must carry
   int any_held;            // some particle is held at its temperature (reading R11)
-  int pf_tiles;            // L2 prefetch distance in tiles (0: none), see prefetch_ahead
   int wall_dirichlet[4];   // x-, x+, y-, y+
   int outflow[4];          // open sides (zero normal gradient; reading R14)
   int np;

@@ -44,11 +44,6 @@ struct BatchParticles {
 // Storage of the populations of the FP32-arithmetic kernels.
 enum : int { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
 
-// Resident CTAs per SM of the single-case step kernel, and the build's L2
-// prefetch distance in occupancy waves (VLB_PREFETCH_WAVES).
-int lattice_step_ctas_per_sm(bool fp64, int storage);
-int lattice_prefetch_waves();
-
 cudaError_t launch_lattice_f32(int mode, const LatticeConst<float>& K, const StepBuffers& B,
                                const ParticleArrays& P, const TileLists& TL, cudaStream_t st, int storage);
 cudaError_t launch_lattice_f64(int mode, const LatticeConst<double>& K, const StepBuffers& B,

@@ -253,48 +253,6 @@ __device__ __forceinline__ C raster_cell(int tx, int ty, int gx, int gy, int np,
 #define VLB_LATTICE_MIN_BLOCKS (1024 / (TILE_X * TILE_Y))
 #endif
 
-// L2 prefetch of the tile one or more occupancy waves ahead.  Each thread
-// loads its cell's 18 populations and S at the start of the CTA and then
-// computes for a long time, so with one cell per thread too few bytes are in
-// flight to cover the DRAM latency.  Tiles run in the order of their linear
-// index, so a CTA asks the L2 for the rows of the tile pf_tiles further on
-// (pf_tiles = SMs x resident CTAs per SM x VLB_PREFETCH_WAVES, set on the
-// host): by the time that tile's CTA starts, its loads are L2 hits.  Warp r
-// takes row r of that tile, lane i < 18 population plane i, lane 18 the S
-// plane, lanes 19 and 20 of warp 0 the tile's particle list (ids and count)
-// in the list buffer this launch reads; one bulk prefetch each (a hint: no data
-// moves into the SM and nothing waits on it).  The sizes stay inside the
-// rows' padded pitch, so every prefetched byte lies in its buffer.
-#ifndef VLB_PREFETCH_WAVES
-#define VLB_PREFETCH_WAVES 0
-#endif
-__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-template <class S, class C>
-__device__ __forceinline__ void prefetch_ahead(const LatticeConst<C>& K, const StepBuffers& B, const TileLists& TL,
-                                               int lin_tile) {
-  if (K.pf_tiles <= 0) return;
-  const int t = lin_tile + K.pf_tiles;
-  if (t >= K.ntx * K.nty) return;
-  const int lane = threadIdx.x;
-  if (lane > 20) return;
-  const int ty = t / K.ntx, tx = t - ty * K.ntx;
-  const int y = ty * TILE_Y + threadIdx.y;
-  if (y >= K.ny) return;
-  const int x0 = tx * TILE_X;
-  const int nel = min(TILE_X, K.pitch - x0);  // a multiple of 16 bytes: see the pitch rule of the layout
-  const long long row = (long long)y * K.pitch + x0;
-  if (lane < 18) {
-    l2_prefetch(static_cast<const S*>(B.src) + (long long)lane * K.plane + row, (unsigned)(nel * sizeof(S)));
-  } else if (lane == 18) {
-    l2_prefetch(static_cast<const C*>(B.s_src) + row, (unsigned)(nel * sizeof(C)));
-  } else if (threadIdx.y == 0) {
-    if (lane == 19) l2_prefetch(TL.ids + (long long)t * TILE_CAP, (unsigned)(TILE_CAP * sizeof(int)));
-    else if ((t | 3) < K.ntx * K.nty) l2_prefetch(TL.count + (t & ~3), 16u);  // the 16-byte group holding count[t]
-  }
-}
-
 // Pull streaming of one cell (Eqs. 3b, 17b) with the wall rules: f-bar and
 // g-bar of x - e_i, or the bounced value at a wall; S of level n.
 template <class S, class C, int MODE>
@@ -669,7 +627,6 @@ __global__ void __launch_bounds__(TILE_X * TILE_Y, sizeof(C) == 4 ? VLB_LATTICE_
 lattice_kernel(const LatticeConst<C> K, const StepBuffers B, const ParticleArrays P, const TileLists TL) {
   __shared__ TileShared<C> sh;
   C f[9], g[9], s_old;
-  if (MODE == MODE_STEP) prefetch_ahead<S, C>(K, B, TL, blockIdx.y * gridDim.x + blockIdx.x);
   pull_direct<S, C, MODE>(K, B, blockIdx.x, blockIdx.y, f, g, s_old);
   cell_body<S, C, MODE, HOLD>(K, B, P, TL, blockIdx.x, blockIdx.y, f, g, s_old, sh, K.band_stamp);
 }
@@ -783,22 +740,6 @@ static cudaError_t launch_mode(int mode, const LatticeConst<C>& K, const StepBuf
   else lattice_kernel<S, C, MODE_MACROS, false><<<grid, block, 0, st>>>(K, B, P, TL);
   return cudaGetLastError();
 }
-
-// Resident CTAs per SM of the step kernel that a handle of this precision and
-// storage launches (0 on error), for the prefetch distance.
-int lattice_step_ctas_per_sm(bool fp64, int storage) {
-  int n = 0;
-  const int threads = TILE_X * TILE_Y;
-  cudaError_t e;
-  if (fp64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lattice_kernel<double, double, MODE_STEP, false>, threads, 0);
-  else if (storage == STORE_F16)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lattice_kernel<__half, float, MODE_STEP, false>, threads, 0);
-  else if (storage == STORE_BF16)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lattice_kernel<__nv_bfloat16, float, MODE_STEP, false>, threads, 0);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lattice_kernel<float, float, MODE_STEP, false>, threads, 0);
-  return e == cudaSuccess ? n : 0;
-}
-int lattice_prefetch_waves() { return VLB_PREFETCH_WAVES; }
 
 cudaError_t launch_lattice_f32(int mode, const LatticeConst<float>& K, const StepBuffers& B,
                                const ParticleArrays& P, const TileLists& TL, cudaStream_t st, int storage) {

@@ -3,8 +3,16 @@
 // resident while they run, and advance together with one batched step
 // (vlb_step_batch) per round; a case that has done its steps is read back
 // (fields and particle state to host memory), freed, and its time to result
-// recorded.  Host code only, on top of the library's public calls; every
-// resident case runs on the server's one CUDA stream.
+// recorded.  Host code only; every resident case runs on the server's one
+// CUDA stream.
+//
+// Nothing in the round loop synchronises the device: a case's buffers come
+// from the server's stream-ordered memory pool (cudaFree would synchronise),
+// the host copy of its error word from a pinned arena made once (page-locked
+// allocations synchronise too), the batch descriptors from one pinned
+// staging block; a finished case's read-back is queued behind its last round
+// into recycled pinned buffers and completed at a later poll, once its event
+// has fired, so the next rounds are already on the GPU meanwhile.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -18,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/vlb.h"
+#include "vlb_internal.h"
 
 namespace {
 
@@ -36,7 +45,19 @@ struct ServeCase {
   std::string error;
   std::vector<double> fields;  // rho, ux, uy, T, fs planes of the last level
   std::vector<double> pstate;  // [n][9]
+  // queued read-back (draining): pinned buffers, event, error-word slot
+  int fbuf = -1, pbuf = -1;
+  cudaEvent_t ev = nullptr;
+  int err_slot = -1;
 };
+
+// A page-locked host buffer of the server's recycled set.
+struct PinnedBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  bool used = false;
+};
+constexpr int kErrSlots = 4096;
 
 }  // namespace
 
@@ -48,6 +69,15 @@ struct vlb_server {
   int64_t next_id = 1;
   std::deque<ServeCase*> queue;
   std::vector<ServeCase*> active;
+  std::vector<ServeCase*> draining;  // read-back queued, not yet complete
+  cudaMemPool_t pool = nullptr;
+  unsigned* err_arena = nullptr;     // kErrSlots pinned error words
+  std::vector<int> free_slots;
+  unsigned char* stage = nullptr;    // batch descriptor staging
+  size_t stage_cap = 0;
+  cudaEvent_t stage_copied = nullptr;
+  std::vector<PinnedBuf> bufs;
+  std::vector<cudaEvent_t> events;   // free events
   std::unordered_map<int64_t, std::unique_ptr<ServeCase>> cases;
   std::chrono::steady_clock::time_point t0;
 
@@ -62,26 +92,83 @@ static vlb_status serve_fail(vlb_server* s, vlb_status st, const std::string& m)
   return st;
 }
 
-// A case stops: read back its result (on success), free its handle and budget.
-static void finish(vlb_server* s, ServeCase* c, vlb_status st, const char* msg) {
-  if (st == VLB_OK) {
-    const size_t cells = (size_t)c->p.nx * c->p.ny;
-    c->fields.assign(5 * cells, 0.0);
-    double* f = c->fields.data();
-    const uint32_t all = VLB_FIELD_RHO | VLB_FIELD_UX | VLB_FIELD_UY | VLB_FIELD_T | VLB_FIELD_FS;
-    st = vlb_get_fields(c->h, all, f, f + cells, f + 2 * cells, f + 3 * cells, f + 4 * cells);
-    if (st == VLB_OK && c->n > 0) {
-      std::vector<double> xy(2 * c->n), th(c->n), uv(2 * c->n), om(c->n), fo(2 * c->n), to(c->n);
-      st = vlb_get_particle_state(c->h, c->n, xy.data(), th.data(), uv.data(), om.data(), fo.data(), to.data());
-      c->pstate.resize((size_t)9 * c->n);
-      for (int k = 0; k < c->n; ++k) {
-        double* r = c->pstate.data() + 9 * (size_t)k;
-        r[0] = xy[2 * k]; r[1] = xy[2 * k + 1]; r[2] = th[k]; r[3] = uv[2 * k]; r[4] = uv[2 * k + 1];
-        r[5] = om[k]; r[6] = fo[2 * k]; r[7] = fo[2 * k + 1]; r[8] = to[k];
-      }
-    }
-    if (st != VLB_OK) msg = vlb_last_error(c->h);
+// A pinned buffer of at least `bytes` from the recycled set (index), or -1.
+static int take_buf(vlb_server* s, size_t bytes) {
+  int best = -1;
+  for (int i = 0; i < (int)s->bufs.size(); ++i)
+    if (!s->bufs[i].used && s->bufs[i].cap >= bytes && (best < 0 || s->bufs[i].cap < s->bufs[best].cap)) best = i;
+  if (best < 0) {
+    PinnedBuf b;
+    b.cap = bytes < 4096 ? 4096 : bytes;
+    if (cudaHostAlloc(&b.p, b.cap, cudaHostAllocDefault) != cudaSuccess) return -1;
+    s->bufs.push_back(b);
+    best = (int)s->bufs.size() - 1;
   }
+  s->bufs[best].used = true;
+  return best;
+}
+
+static void release_case_resources(vlb_server* s, ServeCase* c) {
+  if (c->fbuf >= 0) s->bufs[c->fbuf].used = false;
+  if (c->pbuf >= 0) s->bufs[c->pbuf].used = false;
+  c->fbuf = c->pbuf = -1;
+  if (c->ev) s->events.push_back(c->ev);
+  c->ev = nullptr;
+}
+
+// A case that fails (its device flags stopped it, or it could not be
+// placed): handle freed, budget released (finish_done below).
+static void finish_done(vlb_server* s, ServeCase* c, vlb_status st, const char* msg);
+static void finish(vlb_server* s, ServeCase* c, vlb_status st, const char* msg) { finish_done(s, c, st, msg); }
+
+// Create, fill and initialise the handle of a queued case.  The initial
+// state is built on the handle's own stream, so that admission does not wait
+// for the round running on the server's stream; the handle then moves to it.
+static vlb_status admit(vlb_server* s, ServeCase* c) {
+  vlb_handle_alloc a{s->pool, nullptr};
+  if (!s->free_slots.empty()) {
+    c->err_slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    a.err_host = s->err_arena + c->err_slot;
+  }
+  vlb_status st = vlb_create_in(&c->p, &a, &c->h);
+  if (st != VLB_OK) return st;
+  if (c->n > 0)
+    st = vlb_add_particles(c->h, c->n, c->xy.data(), c->radius.data(), c->T0.data(),
+                           c->has_k ? c->k_ratio.data() : nullptr, nullptr, nullptr);
+  if (st == VLB_OK) st = vlb_step(c->h, 0);  // initial state
+  if (st == VLB_OK) st = vlb_set_stream(c->h, s->stream);
+  return st;
+}
+
+// A case that has done its steps: its read-back queued into pinned buffers
+// behind its last round (completed by complete_draining).
+static void queue_readback(vlb_server* s, ServeCase* c) {
+  const size_t fbytes = 5 * (size_t)c->p.nx * c->p.ny * vlb_value_bytes(c->h);
+  const size_t pbytes = 12 * (size_t)std::max(c->n, 1) * sizeof(double);
+  c->fbuf = take_buf(s, fbytes);
+  c->pbuf = take_buf(s, pbytes);
+  if (!c->ev) {
+    if (!s->events.empty()) {
+      c->ev = s->events.back();
+      s->events.pop_back();
+    } else if (cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess) {
+      c->ev = nullptr;
+    }
+  }
+  vlb_status st = (c->fbuf < 0 || c->pbuf < 0 || !c->ev) ? VLB_ENOMEM : VLB_OK;
+  if (st == VLB_OK)
+    st = vlb_readback_async(c->h, s->bufs[c->fbuf].p, static_cast<double*>(s->bufs[c->pbuf].p), c->ev);
+  if (st != VLB_OK) {
+    finish(s, c, st, vlb_last_error(c->h));
+    return;
+  }
+  s->draining.push_back(c);
+}
+
+// The end of a case whose read-back has completed (or failed): handle freed
+// (its buffers go back to the pool in stream order), budget released.
+static void finish_done(vlb_server* s, ServeCase* c, vlb_status st, const char* msg) {
   if (st != VLB_OK) {
     c->status = st;
     c->error = msg ? msg : "";
@@ -90,28 +177,16 @@ static void finish(vlb_server* s, ServeCase* c, vlb_status st, const char* msg) 
   }
   if (c->h) vlb_destroy(c->h);
   c->h = nullptr;
+  release_case_resources(s, c);
+  if (c->err_slot >= 0) s->free_slots.push_back(c->err_slot);
+  c->err_slot = -1;
   s->used -= c->bytes;
   c->state = st == VLB_OK ? VLB_CASE_DONE : VLB_CASE_FAILED;
   c->t_done = s->now();
-  // host copies of the inputs are no longer needed
   std::vector<double>().swap(c->xy);
   std::vector<double>().swap(c->radius);
   std::vector<double>().swap(c->T0);
   std::vector<double>().swap(c->k_ratio);
-}
-
-// Create, fill and initialise the handle of a queued case.  The initial
-// state is built on the handle's own stream, so that admission does not wait
-// for the round running on the server's stream; the handle then moves to it.
-static vlb_status admit(vlb_server* s, ServeCase* c) {
-  vlb_status st = vlb_create(&c->p, &c->h);
-  if (st != VLB_OK) return st;
-  if (c->n > 0)
-    st = vlb_add_particles(c->h, c->n, c->xy.data(), c->radius.data(), c->T0.data(),
-                           c->has_k ? c->k_ratio.data() : nullptr, nullptr, nullptr);
-  if (st == VLB_OK) st = vlb_step(c->h, 0);  // initial state
-  if (st == VLB_OK) st = vlb_set_stream(c->h, s->stream);
-  return st;
 }
 
 extern "C" {
@@ -144,6 +219,29 @@ vlb_status vlb_serve_create(const vlb_serve_params* sp, vlb_server** out) {
     return VLB_ECUDA;
   }
   s->budget = sp->hbm_budget ? sp->hbm_budget : free_b / 2;
+  // the cases' device memory: a stream-ordered pool of this device that keeps
+  // up to the budget reserved between cases
+  int dev = 0;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  e = cudaGetDevice(&dev);
+  props.location.id = dev;
+  if (e == cudaSuccess) e = cudaMemPoolCreate(&s->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t keep = s->budget;
+    e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->err_arena), kErrSlots * sizeof(unsigned),
+                                          cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    g_serve_error = std::string("server memory pool or pinned arena: ") + cudaGetErrorString(e);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    cudaStreamDestroy(s->stream);
+    delete s;
+    return VLB_ECUDA;
+  }
+  for (int k = kErrSlots - 1; k >= 0; --k) s->free_slots.push_back(k);
   *out = s;
   return VLB_OK;
 }
@@ -174,8 +272,45 @@ vlb_status vlb_serve_submit(vlb_server* s, const vlb_params* p, int32_t n, const
   return VLB_OK;
 }
 
+// Complete the queued read-backs whose events have fired (all of them, in
+// order, when `wait`): results to the case's host vectors, handle freed.
+static void complete_draining(vlb_server* s, bool wait) {
+  std::vector<ServeCase*> keep;
+  for (ServeCase* c : s->draining) {
+    const cudaError_t q = wait ? cudaEventSynchronize(c->ev) : cudaEventQuery(c->ev);
+    if (q == cudaErrorNotReady) {
+      keep.push_back(c);
+      continue;
+    }
+    vlb_status st = q == cudaSuccess ? vlb_check_flags(c->h) : VLB_ECUDA;  // the device flags of the last steps
+    const char* msg = st == VLB_OK ? nullptr : (q == cudaSuccess ? vlb_last_error(c->h) : cudaGetErrorString(q));
+    if (st == VLB_OK) {
+      const size_t cells = (size_t)c->p.nx * c->p.ny;
+      c->fields.resize(5 * cells);
+      const void* f = s->bufs[c->fbuf].p;
+      if (vlb_value_bytes(c->h) == 8) std::memcpy(c->fields.data(), f, 5 * cells * sizeof(double));
+      else {
+        const float* ff = static_cast<const float*>(f);
+        for (size_t k = 0; k < 5 * cells; ++k) c->fields[k] = ff[k];
+      }
+      if (c->n > 0) {
+        const double* ps = static_cast<const double*>(s->bufs[c->pbuf].p);
+        const size_t n = (size_t)c->n;
+        c->pstate.resize(9 * n);
+        const int cols[9] = {0, 1, 2, 3, 4, 5, 9, 10, 11};  // x y theta ux uy omega F_c,x F_c,y T_c
+        for (size_t k = 0; k < n; ++k)
+          for (int q9 = 0; q9 < 9; ++q9) c->pstate[9 * k + q9] = ps[cols[q9] * n + k];
+      }
+    }
+    finish_done(s, c, st, msg);
+  }
+  s->draining.swap(keep);
+}
+
 vlb_status vlb_serve_poll(vlb_server* s, int32_t* nqueued, int32_t* nactive, int32_t* ndone) {
   if (!s) return VLB_EINVAL;
+  // 0. results of earlier rounds whose read-back has arrived
+  complete_draining(s, false);
   // 1. one round, queued on the server's stream: every resident case advances
   //    by the same number of steps, at most steps_per_round and at most what
   //    the nearest case still needs
@@ -188,7 +323,8 @@ vlb_status vlb_serve_poll(vlb_server* s, int32_t* nqueued, int32_t* nactive, int
       hs.clear();
       for (ServeCase* c : s->active) hs.push_back(c->h);
       int32_t failed = -1;
-      const vlb_status st = vlb_step_batch(hs.data(), (int32_t)hs.size(), (int32_t)chunk, &failed);
+      const vlb_status st = vlb_step_batch_staged(hs.data(), (int32_t)hs.size(), (int32_t)chunk, &failed, &s->stage,
+                                                  &s->stage_cap, &s->stage_copied);
       if (st == VLB_OK) break;
       if (failed < 0 || st == VLB_ECUDA) return serve_fail(s, st, vlb_last_error(failed >= 0 ? hs[failed] : nullptr));
       // a case whose device flags stopped it leaves; the others have not moved
@@ -212,22 +348,26 @@ vlb_status vlb_serve_poll(vlb_server* s, int32_t* nqueued, int32_t* nactive, int
     c->state = VLB_CASE_ACTIVE;
     const vlb_status st = admit(s, c);
     if (st != VLB_OK) finish(s, c, st, c->h ? vlb_last_error(c->h) : vlb_last_error(nullptr));
-    else if (c->nsteps == 0) finish(s, c, VLB_OK, nullptr);
+    else if (c->nsteps == 0) queue_readback(s, c);
     else admitted.push_back(c);
   }
-  // 3. the cases that have done their steps: results to host, then freed
+  // 3. the cases that have done their steps: read-back queued behind the round
   std::vector<ServeCase*> keep;
   for (ServeCase* c : s->active) {
-    if (c->done_steps == c->nsteps) finish(s, c, VLB_OK, nullptr);
+    if (c->done_steps == c->nsteps) queue_readback(s, c);
     else keep.push_back(c);
   }
   for (ServeCase* c : admitted) keep.push_back(c);
   s->active.swap(keep);
+  // 4. nothing left to queue: wait for the read-backs instead of spinning
+  if (s->active.empty() && (s->queue.empty() || admitted.empty()) && !s->draining.empty() &&
+      (s->queue.empty() || s->used + s->queue.front()->bytes > s->budget))
+    complete_draining(s, true);
   int32_t done = 0;
   for (auto& kv : s->cases)
     if (kv.second->state == VLB_CASE_DONE || kv.second->state == VLB_CASE_FAILED) ++done;
   if (nqueued) *nqueued = (int32_t)s->queue.size();
-  if (nactive) *nactive = (int32_t)s->active.size();
+  if (nactive) *nactive = (int32_t)(s->active.size() + s->draining.size());
   if (ndone) *ndone = done;
   return VLB_OK;
 }
@@ -276,11 +416,25 @@ const char* vlb_serve_last_error(const vlb_server* s) { return s ? s->err.c_str(
 
 void vlb_serve_destroy(vlb_server* s) {
   if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
   for (ServeCase* c : s->active)
     if (c->h) vlb_destroy(c->h);
+  for (ServeCase* c : s->draining)
+    if (c->h) vlb_destroy(c->h);
   if (s->stream) {
-    cudaStreamSynchronize(s->stream);
+    cudaStreamSynchronize(s->stream);  // the handles' stream-ordered frees
     cudaStreamDestroy(s->stream);
+  }
+  for (auto& kv : s->cases)
+    if (kv.second->ev) cudaEventDestroy(kv.second->ev);
+  for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+  if (s->stage_copied) cudaEventDestroy(s->stage_copied);
+  if (s->stage) cudaFreeHost(s->stage);
+  for (PinnedBuf& b : s->bufs) cudaFreeHost(b.p);
+  if (s->err_arena) cudaFreeHost(s->err_arena);
+  if (s->pool) {
+    cudaDeviceSynchronize();  // frees queued on the cases' own streams
+    cudaMemPoolDestroy(s->pool);
   }
   delete s;
 }

@@ -8,8 +8,7 @@ def test_tuner_records_the_fastest_shape(tmp_path):
     from paper_2410_23802_gb300 import autotune as A, build as B
     path = str(tmp_path / "tuned.json")
     built = []
-    times = {"tune_y4_w1": 1.30, "tune_y4_w0": 1.32, "tune_y4_w2": 1.31, "tune_y2_w1": 1.25, "tune_y8_w1": 1.40,
-             "tune_y4_b6_w1": 1.35}
+    times = {"tune_y4": 1.30, "tune_y2": 1.25, "tune_y8": 1.40, "tune_y4_b6": 1.35}
 
     def fake_build(defines, out):
         built.append((tuple(defines), out))
@@ -20,26 +19,25 @@ def test_tuner_records_the_fastest_shape(tmp_path):
 
     rec = A.tune("channels", steps=7, path=path, build=fake_build, timer=fake_timer)
     assert len(built) == len(A.CANDIDATES) == len({b[1] for b in built})
-    y2 = ["VLB_TILE_Y=2", "VLB_PREFETCH_WAVES=1"]
+    y2 = ["VLB_TILE_Y=2"]
     assert rec["channels"]["defines"] == y2 and rec["use"] == "channels"
     assert B.tuned_defines(path) == y2
     # a second workload recorded without taking over the build's choice
-    times["tune_y8_w1"] = 0.5
+    times["tune_y8"] = 0.5
     rec = A.tune("cavity", steps=7, path=path, use=False, build=fake_build, timer=fake_timer)
-    assert rec["cavity"]["defines"] == ["VLB_TILE_Y=8", "VLB_PREFETCH_WAVES=1"] and rec["use"] == "channels"
+    assert rec["cavity"]["defines"] == ["VLB_TILE_Y=8"] and rec["use"] == "channels"
     assert B.tuned_defines(path) == y2
     r = json.load(open(path))["cavity"]["results"]
-    assert abs(r[4]["mlups"] - 1000 / 0.5e-3 / 1e6) < 1e-12
+    assert abs(r[2]["mlups"] - 1000 / 0.5e-3 / 1e6) < 1e-12
 
 
 def test_candidates_are_valid_builds():
     from paper_2410_23802_gb300 import autotune as A
     tags = set()
-    for ty, mb, waves in A.CANDIDATES:
+    for ty, mb in A.CANDIDATES:
         assert ty in (1, 2, 4, 8) and 32 * ty <= 1024
         assert mb is None or 1 <= mb <= 1024 // (32 * ty)
-        assert waves in (0, 1, 2, 3)
-        tags.add(A.candidate_tag(A.candidate_defines(ty, mb, waves)))
+        tags.add(A.candidate_tag(A.candidate_defines(ty, mb)))
     assert len(tags) == len(A.CANDIDATES)
 
 

@@ -71,14 +71,14 @@ def _errors(name):
 
 
 BAR = {"u": 1e-3, "T": 1e-3, "v": 1e-2}
-# measured with round-to-nearest storage: fp16 u 2.3e-4, T 9.6e-5, v 2.6e-4; bf16 u 1.49e-3, T 9.5e-4, v 2.4e-3
-REGRESSION = {"fp16": {"u": 5e-4, "T": 2e-4, "v": 1e-3}, "bf16": {"u": 3e-3, "T": 2e-3, "v": 5e-3}}
+# measured (stochastic rounding): fp16 u 2.27e-4, T 4.8e-5, v 1.4e-4; bf16 u 1.8e-3 (misses), T 3.9e-4, v 1.0e-3
+REGRESSION = {"fp16": {"u": 5e-4, "T": 1e-4, "v": 5e-4}, "bf16": {"u": 4e-3, "T": 8e-4, "v": 2e-3}}
 
 
 def _cases():
     for name in ("fp16", "bf16"):
         for q in ("u", "T", "v"):
-            marks = [pytest.mark.xfail(strict=False, reason="BF16 significand noise")] if (name, q) == ("bf16", "u") else []
+            marks = [pytest.mark.xfail(strict=True, reason="BF16 significand noise")] if (name, q) == ("bf16", "u") else []
             yield pytest.param(name, q, marks=marks, id=f"{name}-{q}")
 
 
