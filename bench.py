@@ -342,6 +342,24 @@ def _channel_lattices(V, cases, streams):
     return lats
 
 
+def _persistent_batches() -> bool:
+    from paper_2410_23802_gb300 import build as B
+    return "VLB_BATCH_PERSISTENT=0" not in B.tuned_defines()
+
+
+def _batch_form() -> str:
+    if _persistent_batches():
+        return "one persistent launch per step (tiles, then the next level's particle steps), CUDA-graph replay"
+    return "a CTA per tile and a particle kernel per step"
+
+
+def _batch_launches(steps: int) -> int:
+    """Kernels of one vlb_step_batch call of `steps` steps over one kernel
+    variant without ellipses: the level-0 particle step, steps - 1 persistent
+    launches and the last level's tiles; or two per step."""
+    return steps + 1 if _persistent_batches() else 2 * steps
+
+
 def measure_batched(V, local, n_cases, steps, warmup, precision="fp32"):
     """The 256-channel configuration resident at once: K steps of all cases
     with vlb_step_batch (one launch of each kernel per step for every case),
@@ -395,7 +413,8 @@ def measure_batched(V, local, n_cases, steps, warmup, precision="fp32"):
                       "note": "one stream, one case after the other with vlb_step"},
             "vs_plain": round(plain_ms / batched_ms, 3),
             "workload": f"{len(cases)} channels W~U{{64..256}} x 4W, 1 disk each, {cells} cells, {precision}",
-            "steps": steps, "warmup": warmup, "gpu_launches": 2 * steps, "clocks": clocks}
+            "steps": steps, "warmup": warmup, "gpu_launches": _batch_launches(steps), "form": _batch_form(),
+            "clocks": clocks}
 
 
 def _serve_stream(n_cases, steps):

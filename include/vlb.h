@@ -54,7 +54,7 @@ typedef enum {
   VLB_ESTATE = -4,     /* call not allowed in the handle's current state */
   VLB_EUNSTABLE = -5,  /* NaN, a particle too fast, or a particle out of the domain */
   VLB_EOVERFLOW = -6,  /* a fixed-capacity list (owners, tile lists, contacts) overflowed */
-  VLB_ETIMEOUT = -7    /* reserved for bounded device-side waits */
+  VLB_ETIMEOUT = -7    /* a bounded device-side wait ran out (vlb_step_batch) */
 } vlb_status;
 
 /* Arithmetic and storage precision of the lattice populations. */
@@ -133,12 +133,15 @@ vlb_status vlb_create(const vlb_params* p, vlb_handle** out);
 
 /* Hold particles [first, first + n) at their temperature T0 (held[k] != 0)
  * or let them conduct (held[k] == 0, the default): in the held-temperature
- * sedimentation case of Sec. 3.3 the particle stays at T_c.  Reading: in
- * the part of a cell such a particle covers, the thermal populations are
- * replaced by the equilibrium at T0 in the volumetric form of Eq. 8,
- * g = (1 - f_fix) g + sum_p f_s,p g^eq(c_vs T0_p, T0_p).  Only before the
- * first vlb_step (VLB_ESTATE afterwards); VLB_EINVAL for a range outside the
- * particles added so far. */
+ * sedimentation case of Sec. 3.3 the particle stays at T_c; the paper does
+ * not say how.  held[k] == 1 (reading R11): in the part of a cell such a
+ * particle covers, the thermal populations are replaced by the equilibrium
+ * at T0 in the volumetric form of Eq. 8,
+ * g = (1 - f_fix) g + sum_p f_s,p g^eq(c_vs T0_p, T0_p).  held[k] == 2
+ * (reading R11b): every cell the particle owns takes that equilibrium whole
+ * (weight 1 in place of f_s,p; several such owners share the cell equally).
+ * Other non-zero values mean 1.  Only before the first vlb_step (VLB_ESTATE
+ * afterwards); VLB_EINVAL for a range outside the particles added so far. */
 vlb_status vlb_set_fixed_temperature(vlb_handle* h, int32_t first, int32_t n, const int32_t* held);
 
 /* Queue all further work of h on cuda_stream (a cudaStream_t; NULL selects
@@ -199,9 +202,16 @@ vlb_status vlb_insert_particles(vlb_handle* h, int32_t n, const double* xy, cons
 vlb_status vlb_step(vlb_handle* h, int32_t nsteps);
 
 /* nsteps time steps of each of n handles (independent cases of any sizes,
- * e.g. many small channels) with one launch of each kernel per step for all
- * of them (one lattice launch per distinct precision / storage / held-path
- * combination).  Each handle advances exactly as vlb_step(h, nsteps) would,
+ * e.g. many small channels) with one persistent launch per step for all of
+ * them (one per distinct precision / storage / held-path combination): a
+ * grid of the GPU's resident capacity whose CTAs take, in order from a
+ * device counter, the lattice tiles of every case and then the particle
+ * steps of the next level, each particle after a bounded wait for the last
+ * tile of its own case.  The launches of one step are the same every step:
+ * they are captured once per call into a CUDA graph and replayed (plain
+ * launches on the legacy default stream, which cannot be captured).  A wait
+ * that runs out (VLB_ETIMEOUT on that handle) leaves the context usable.
+ * Each handle advances exactly as vlb_step(h, nsteps) would,
  * bit for bit, and single steps and batch calls may alternate.  The work is
  * queued on hs[0]'s stream after the work already queued on every handle's
  * stream; every handle's stream then waits for it, so later calls on any
@@ -218,6 +228,16 @@ vlb_status vlb_step(vlb_handle* h, int32_t nsteps);
  * vlb_step.  Not part of the paper: it batches the paper's time step over
  * cases. */
 vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed);
+
+/* Test hook of the bounded waits of vlb_step_batch: wait_ns is the limit of
+ * each device-side wait (<= 0: the default, one second; a normal wait lasts
+ * less than one lattice pass).  stuck_handle >= 0 names a position in the
+ * handle array of later vlb_step_batch calls whose particle steps then wait
+ * for a tile count that is never reached, so that those waits run out: the
+ * handle's next call returns VLB_ETIMEOUT (its state is no longer valid), the
+ * other handles and the context are unaffected.  -1 turns it off.
+ * Process-wide.  VLB_EINVAL for stuck_handle < -1. */
+vlb_status vlb_debug_batch_wait(int64_t wait_ns, int32_t stuck_handle);
 
 /* Block until the handle's queued work is done; returns the first recorded
  * device-side failure, else VLB_OK. */

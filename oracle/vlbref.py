@@ -642,13 +642,16 @@ def geq(eps, T, cref):
 
 def fixed_temperature_correction(g, ras, T_p, fixed, cv_s, cref):
     """Particles held at their own temperature (Sec. 3.3, where the particle
-    stays at the cold temperature T_c throughout; reading R11): in
-    the part of a cell that such a particle covers, the thermal populations
-    are replaced by the equilibrium at the particle's temperature, in the
-    volumetric form of Eq. 8:
-        g = (1 - f_fix) g + sum_{p fixed} f_s,p g^eq(c_vs T_p, T_p),
-    f_fix = sum_{p fixed} f_s,p.  Particles not held (fixed[p] False) keep
-    the conjugate treatment."""
+    stays at the cold temperature T_c throughout).  fixed[p] = 1 (reading
+    R11): in the part of a cell that such a particle covers, the thermal
+    populations are replaced by the equilibrium at the particle's
+    temperature, in the volumetric form of Eq. 8:
+        g = (1 - f_fix) g + sum_{p held} f_s,p g^eq(c_vs T_p, T_p),
+    f_fix = sum_{p held} f_s,p.  fixed[p] = 2 (reading R11b): every cell the
+    particle owns takes that equilibrium whole (weight 1 in place of f_s,p;
+    weights summing above 1 are scaled to 1).  Particles not held
+    (fixed[p] = 0) keep the conjugate treatment."""
+    fixed = np.asarray(fixed).astype(np.int64)
     ffix = np.zeros(g.shape[1:])
     acc = np.zeros_like(g)
     for k in range(MAX_OWNERS):
@@ -656,12 +659,16 @@ def fixed_temperature_correction(g, ras, T_p, fixed, cv_s, cref):
         if not sel.any():
             continue
         own = np.where(sel, ras.owner[:, :, k], 0)
-        w = np.where(sel & fixed[own], ras.fsp[:, :, k], 0.0)
+        mode = np.where(sel, fixed[own], 0)
+        w = np.where(mode == 1, ras.fsp[:, :, k], np.where(mode == 2, 1.0, 0.0))
         if not w.any():
             continue
         Tp = T_p[own]
         ffix = ffix + w
         acc = acc + w * geq(cv_s * Tp, Tp, cref)
+    over = ffix > 1.0
+    acc = np.where(over[None], acc / np.where(over, ffix, 1.0)[None], acc)
+    ffix = np.minimum(ffix, 1.0)
     return (1.0 - ffix) * g + acc
 
 
@@ -873,8 +880,8 @@ class Simulation:
         self.prm = prm
         n = len(x)
         z = np.zeros(n)
-        # particles held at their initial temperature T0 (reading R11)
-        self.fixed_T = np.array(fixed_T if fixed_T is not None else np.zeros(n), dtype=bool)
+        # particles held at their initial temperature T0: 1 reading R11, 2 R11b
+        self.fixed_T = np.array(fixed_T if fixed_T is not None else np.zeros(n), dtype=np.int64)
         self.part = {
             "x": np.array(x, dtype=float), "y": np.array(y, dtype=float),
             "r": np.array(radius, dtype=float), "T0": np.array(T0, dtype=float),
@@ -1010,7 +1017,7 @@ class Simulation:
         P["uy_prev"] = np.concatenate([P["uy_prev"], np.asarray(new["uy"], dtype=float)])
         P["omega_prev"] = np.concatenate([P["omega_prev"], np.asarray(new["omega"], dtype=float)])
         self._set_inertia()
-        self.fixed_T = np.concatenate([self.fixed_T, np.zeros(n, dtype=bool)])
+        self.fixed_T = np.concatenate([self.fixed_T, np.zeros(n, dtype=np.int64)])
         self.F_mes = np.concatenate([self.F_mes, np.zeros((n, 2))])
         self.T_mes = np.concatenate([self.T_mes, z])
         self.Fc = np.concatenate([self.Fc, np.zeros((n, 2))])
@@ -1214,7 +1221,7 @@ def vlbref_add_particles(h, n, xy, radius, T0, k_ratio=None, uv=None, omega=None
         P["ux"].append(float(uv[2 * k]) if uv is not None else 0.0)
         P["uy"].append(float(uv[2 * k + 1]) if uv is not None else 0.0)
         P["omega"].append(float(omega[k]) if omega is not None else 0.0)
-        P["fixed"].append(False)
+        P["fixed"].append(0)
         P["b"].append(r)
         P["theta"].append(0.0)
     return VLBREF_OK
@@ -1248,7 +1255,7 @@ def vlbref_set_fixed_temperature(h, first, n, held):
     if first < 0 or n < 0 or first + n > len(h.parts["x"]):
         return h.fail(VLBREF_EINVAL, "particle range")
     for k in range(n):
-        h.parts["fixed"][first + k] = bool(held[k])
+        h.parts["fixed"][first + k] = int(held[k]) if held[k] in (0, 1, 2) else 1
     return VLBREF_OK
 
 

@@ -1,8 +1,11 @@
 """Autotuner of the lattice kernel's build-time shape.
 
 The tile height (VLB_TILE_Y: CTAs of 32 x TILE_Y threads, one per tile of as
-many cells) and the bound on resident CTAs per SM that sets the register
-budget (VLB_LATTICE_MIN_BLOCKS) are compile-time constants of the kernels.
+many cells), the bound on resident CTAs per SM that sets the register
+budget (VLB_LATTICE_MIN_BLOCKS) and, for batches, the form of the batched
+step (VLB_BATCH_PERSISTENT: a persistent launch per step replayed from a
+CUDA graph, or a CTA per tile plus a particle kernel per step) are
+compile-time constants of the kernels.
 The tuner builds the library once per candidate shape (each into a file of
 its own), times a workload with each build in a fresh process on the GPU,
 and records every result and the fastest shape in tuned.json, which
@@ -25,18 +28,27 @@ import sys
 
 from . import build as B
 
-# (tile height, CTAs per SM the registers are budgeted for; None: 1024 threads per SM)
-CANDIDATES = [(4, None), (2, None), (8, None), (4, 6)]
+# (tile height, CTAs per SM the registers are budgeted for (None: 1024 threads
+# per SM), persistent batched step (None: the default, on; 0: off))
+CANDIDATES = [(4, None, None), (2, None, None), (8, None, None), (4, 6, None), (4, None, 0), (8, None, 0)]
 
 
-def candidate_defines(tile_y: int, min_blocks: int | None) -> list[str]:
+def candidates(workload: str) -> list[tuple]:
+    """The shapes timed for a workload: the batched-step form matters only
+    for batches."""
+    return [c for c in CANDIDATES if workload == "channels" or c[2] is None]
+
+
+def candidate_defines(tile_y: int, min_blocks: int | None, persistent: int | None = None) -> list[str]:
     d = [f"VLB_TILE_Y={tile_y}"]
     if min_blocks is not None:
         d.append(f"VLB_LATTICE_MIN_BLOCKS={min_blocks}")
+    if persistent is not None:
+        d.append(f"VLB_BATCH_PERSISTENT={persistent}")
     return d
 
 
-_SHORT = {"VLB_TILE_Y": "y", "VLB_LATTICE_MIN_BLOCKS": "b"}
+_SHORT = {"VLB_TILE_Y": "y", "VLB_LATTICE_MIN_BLOCKS": "b", "VLB_BATCH_PERSISTENT": "p"}
 
 
 def candidate_tag(defines: list[str]) -> str:
@@ -95,8 +107,8 @@ def tune(workload: str, steps: int = 200, path: str = B.TUNED, use: bool = True,
     build = build or (lambda defines, out: B.build(defines=defines, out=out))
     timer = timer or time_candidate
     results = []
-    for tile_y, mb in CANDIDATES:
-        defines = candidate_defines(tile_y, mb)
+    for tile_y, mb, pers in candidates(workload):
+        defines = candidate_defines(tile_y, mb, pers)
         lib = os.path.join(B.BUILD, candidate_tag(defines) + ".so")
         build(defines, lib)
         r = timer(lib, workload, steps)

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libvlb.so")
-SOURCES = ["vlb_lattice.cu", "vlb_particles.cu", "vlb_capi.cu", "vlb_noalloc.cu", "vlb_serve.cu"]
+SOURCES = ["vlb_lattice.cu", "vlb_particles.cu", "vlb_batch.cu", "vlb_capi.cu", "vlb_noalloc.cu", "vlb_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -134,6 +134,8 @@ static vlb_status device_flags(vlb_handle* h) {
   if (e & ERR_OUT_OF_DOMAIN) m += " particle out of the domain;";
   if (e & ERR_TOO_FAST) m += " particle faster than 0.5 lu/step;";
   if (e & ERR_NAN) m += " NaN population;";
+  if (e & ERR_TIMEOUT) m += " a device-side wait of the persistent batched step ran out;";
+  if (e & ERR_TIMEOUT) return fail(h, VLB_ETIMEOUT, m);
   const bool unstable = e & (ERR_OUT_OF_DOMAIN | ERR_TOO_FAST | ERR_NAN);
   return fail(h, unstable ? VLB_EUNSTABLE : VLB_EOVERFLOW, m);
 }
@@ -292,7 +294,7 @@ static double min_image(double d, int L, int periodic) {
 static size_t particle_block_bytes(size_t capn) {
   return 16 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) + a256(capn * sizeof(int)) +
          a256(capn * NBR_CAP * sizeof(int)) + a256(capn * sizeof(int)) + a256(capn * 8 * sizeof(double)) +
-         a256(capn * sizeof(RasterRec));
+         a256(capn * sizeof(int)) + a256(capn * sizeof(RasterRec));
 }
 static int band_offset(double rmax) { return (int)std::ceil(rmax) + 2; }
 constexpr int AUDIT_BLOCKS = 608;  // 4 x 152 SMs
@@ -393,6 +395,7 @@ vlb_status vlb_create_in(const vlb_params* pp, const vlb_handle_alloc* alloc, vl
     h->P.nbr = reinterpret_cast<int*>(b); b += a256(capn * NBR_CAP * sizeof(int));
     h->P.fixed_T = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.pk = reinterpret_cast<double*>(b); b += a256(capn * 8 * sizeof(double));
+    h->P.pending = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.rec = reinterpret_cast<RasterRec*>(b);
   }
   cudaMemsetAsync(h->pbase, 0, pbytes, h->stream);
@@ -417,7 +420,7 @@ vlb_status vlb_set_fixed_temperature(vlb_handle* h, int32_t first, int32_t n, co
   if (h->initialized) return fail(h, VLB_ESTATE, "fixed temperatures must be set before the first step");
   if (first < 0 || n < 0 || first + n > h->np || (n > 0 && !held))
     return fail(h, VLB_EINVAL, "vlb_set_fixed_temperature: particle range outside the added particles");
-  for (int k = 0; k < n; ++k) h->hfix[first + k] = held[k] != 0;
+  for (int k = 0; k < n; ++k) h->hfix[first + k] = held[k] == 2 ? 2 : (held[k] != 0 ? 1 : 0);
   return VLB_OK;
 }
 
@@ -663,6 +666,73 @@ static vlb_status step_once(vlb_handle* h) {
   return VLB_OK;
 }
 
+// Steps with the particle steps folded into the lattice launches (build
+// option VLB_FOLD_PARTICLES, on by default; cases without ellipses, whose
+// FP64 band pass keeps a kernel of its own): the particle step of level 0,
+// nsteps - 1 launches of lattice_folded_kernel (level s and the particle steps
+// of level s + 1), the last level's lattice_kernel.  The level buffers, list
+// buffers and stamps advance as nsteps calls of step_once would advance them,
+// so the two forms give the same bits and may alternate.
+#ifndef VLB_FOLD_PARTICLES
+#define VLB_FOLD_PARTICLES 1
+#endif
+constexpr bool kFoldParticles = VLB_FOLD_PARTICLES != 0;
+
+static vlb_status steps_folded(vlb_handle* h, int nsteps) {
+  int nl = 1 - h->tl;
+  next_band_stamp(h);
+  CK(h, launch_particle_step(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
+  // the buffer the particle steps of level 1 append to still holds the lists
+  // of the level before this call
+  CK(h, cudaMemsetAsync(h->TL[1 - nl].count, 0, (size_t)h->ntx * h->nty * sizeof(int), h->stream));
+  for (int k = 0; k + 1 < nsteps; ++k) {
+    StepBuffers B;
+    B.src = h->pop[h->cur];
+    B.dst = h->pop[1 - h->cur];
+    B.s_src = h->spl[h->cur];
+    B.s_dst = h->spl[1 - h->cur];
+    B.macro = h->macro;
+    B.err = h->err_dev;
+    TileLists TL = h->TL[nl];
+    TL.next_count = nullptr;  // read, then cleared tile by tile
+    TileLists TLn = h->TL[1 - nl];
+    TLn.next_count = nullptr;
+    ParticleConst PC = h->PC;
+    PC.band_stamp = band_stamp_after(h->PC.band_stamp, 1);
+    const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
+    if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
+    cudaError_t e = h->p.precision == VLB_FP64
+                        ? launch_lattice_folded_f64(h->K64, B, h->P, TL, PC, TLn, h->stream)
+                        : launch_lattice_folded_f32(h->K32, B, h->P, TL, PC, TLn, h->stream, h->storage);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lattice kernel");
+    if (rec) {
+      CK(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+      h->ev_used += 2;
+    }
+    h->tl = nl;
+    h->cur = 1 - h->cur;
+    ++h->step;
+    h->macros_valid = false;
+    next_band_stamp(h);  // the stamp of the level the folded particle steps made
+    nl = 1 - nl;
+  }
+  // the last level: lattice_kernel, which clears the other list buffer for
+  // the next call's first particle step
+  const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
+  if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
+  vlb_status s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur, nl);
+  if (s != VLB_OK) return s;
+  if (rec) {
+    CK(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
+    h->ev_used += 2;
+  }
+  h->tl = nl;
+  h->cur = 1 - h->cur;
+  ++h->step;
+  h->macros_valid = false;
+  return VLB_OK;
+}
+
 vlb_status vlb_insert_particles(vlb_handle* h, int32_t n, const double* xy, const double* radius, const double* T0,
                                 const double* k_ratio, const double* uv, const double* omega) {
   if (!h) return VLB_EINVAL;
@@ -733,8 +803,12 @@ vlb_status vlb_step(vlb_handle* h, int32_t nsteps) {
   vlb_status s = device_flags(h);
   if (s != VLB_OK) return s;
   if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
-  for (int k = 0; k < nsteps; ++k)
-    if ((s = step_once(h)) != VLB_OK) return s;
+  if (kFoldParticles && nsteps >= 2 && h->PC.any_ellipse == 0) {
+    if ((s = steps_folded(h, nsteps)) != VLB_OK) return s;
+  } else {
+    for (int k = 0; k < nsteps; ++k)
+      if ((s = step_once(h)) != VLB_OK) return s;
+  }
   CK(h, pull_flags(h));
   return VLB_OK;
 }
@@ -752,9 +826,43 @@ struct BatchGroup {
   std::vector<int> handles;  // indices into the call's handle array
   size_t desc_off = 0, table_off = 0;
   int ntiles = 0;
+  // the persistent form: (case of the group, particle) items, the handle of
+  // each case, the work counters and the tiles done per case
+  std::vector<int2> pitems;
+  size_t pitems_off = 0, chandle_off = 0, ctl_off = 0, done_off = 0;
+  int grid = 0;
 };
 
+// Test hook of the persistent step's bounded waits (vlb_debug_batch_wait).
+long long g_wait_ns = 1000000000ll;  // one second
+int g_stuck_handle = -1;
+
 size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
+
+// The batched step in its persistent form (build option VLB_BATCH_PERSISTENT,
+// on by default), else one CTA per tile and a particle kernel per level.
+#ifndef VLB_BATCH_PERSISTENT
+#define VLB_BATCH_PERSISTENT 1
+#endif
+constexpr bool kPersistent = VLB_BATCH_PERSISTENT != 0;
+
+template <class C>
+void fill_persistent(PersistentBatch<C>& A, unsigned char* dev, const BatchGroup& g, const BatchParticles* d_part,
+                     bool with_particles, int stuck) {
+  A.cases = reinterpret_cast<const BatchLattice<C>*>(dev + g.desc_off);
+  A.tile_case = reinterpret_cast<const int*>(dev + g.table_off);
+  A.pcases = d_part;
+  A.case_handle = reinterpret_cast<const int*>(dev + g.chandle_off);
+  A.pitems = reinterpret_cast<const int2*>(dev + g.pitems_off);
+  A.ctl = reinterpret_cast<BatchCtl*>(dev + g.ctl_off);
+  A.done = reinterpret_cast<int*>(dev + g.done_off);
+  A.ntiles = g.ntiles;
+  A.npitems = (int)g.pitems.size();
+  A.ncases = (int)g.handles.size();
+  A.with_particles = with_particles ? 1 : 0;
+  A.stuck_case = stuck;
+  A.wait_ns = g_wait_ns;
+}
 
 template <class C>
 void fill_lattice_desc(vlb_handle* h, const LatticeConst<C>& K, int tile0, BatchLattice<C>& d) {
@@ -820,6 +928,7 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
   }
 
   // ---- descriptors -----------------------------------------------------------
+  const int h0dev = hs[0]->device;
   std::vector<BatchGroup> groups;
   std::vector<int2> items;
   for (int i = 0; i < n; ++i) {
@@ -852,6 +961,20 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
     bytes = align16(bytes + (g.f64 ? sizeof(BatchLattice<double>) : sizeof(BatchLattice<float>)) * g.handles.size());
     g.table_off = bytes;
     bytes = align16(bytes + sizeof(int) * nt);
+    if (kPersistent) {
+      for (size_t c = 0; c < g.handles.size(); ++c)
+        for (int k = 0; k < hs[g.handles[c]]->np; ++k) g.pitems.push_back(make_int2((int)c, k));
+      g.pitems_off = bytes;
+      bytes = align16(bytes + sizeof(int2) * g.pitems.size());
+      g.chandle_off = bytes;
+      bytes = align16(bytes + sizeof(int) * g.handles.size());
+      g.ctl_off = bytes;
+      bytes = align16(bytes + sizeof(BatchCtl));
+      g.done_off = bytes;
+      bytes = align16(bytes + sizeof(int) * g.handles.size());
+      g.grid = persistent_grid(h0dev, g.f64, g.storage, g.held);
+      if (g.grid <= 0) return bad(g.handles[0], fail(hs[g.handles[0]], VLB_ECUDA, "vlb_step_batch: occupancy query"));
+    }
   }
   // the staging block of the previous call (led by hs[0], or the caller's)
   // is free once its copy ran
@@ -897,6 +1020,11 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
       for (int t = 0; t < nt; ++t) table[tile0 + t] = (int)c;
       tile0 += nt;
     }
+    if (kPersistent) {
+      if (!g.pitems.empty()) std::memcpy(hostp + g.pitems_off, g.pitems.data(), sizeof(int2) * g.pitems.size());
+      int* ch = reinterpret_cast<int*>(hostp + g.chandle_off);
+      for (size_t c = 0; c < g.handles.size(); ++c) ch[c] = g.handles[c];
+    }
   }
 
   // ---- launches on the first handle's stream, joined with the others ---------
@@ -916,16 +1044,66 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
   const int nitems = (int)items.size();
   bool any_ellipse = false;
   for (int i = 0; i < n; ++i) any_ellipse |= hs[i]->PC.any_ellipse != 0;
-  for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
-    e = launch_particle_step_batch(d_part, d_items, nitems, k, any_ellipse, bs);
-    for (auto& g : groups) {
-      if (e != cudaSuccess) break;
-      const int* table = reinterpret_cast<const int*>(dev + g.table_off);
-      e = g.f64 ? launch_lattice_batch_f64(reinterpret_cast<const BatchLattice<double>*>(dev + g.desc_off), table,
-                                           g.ntiles, k, g.held, bs)
-                : launch_lattice_batch_f32(reinterpret_cast<const BatchLattice<float>*>(dev + g.desc_off), table,
-                                           g.ntiles, k, g.storage, g.held, bs);
+  if (!kPersistent) {
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+      e = launch_particle_step_batch(d_part, d_items, nitems, k, any_ellipse, bs);
+      for (auto& g : groups) {
+        if (e != cudaSuccess) break;
+        const int* table = reinterpret_cast<const int*>(dev + g.table_off);
+        e = g.f64 ? launch_lattice_batch_f64(reinterpret_cast<const BatchLattice<double>*>(dev + g.desc_off), table,
+                                             g.ntiles, k, g.held, bs)
+                  : launch_lattice_batch_f32(reinterpret_cast<const BatchLattice<float>*>(dev + g.desc_off), table,
+                                             g.ntiles, k, g.storage, g.held, bs);
+      }
     }
+  } else if (e == cudaSuccess) {
+    // particle step of level 0; then nsteps - 1 persistent launches per group
+    // of tiles of level s and particle steps of level s + 1 (the same launches
+    // every level: captured once into a CUDA graph and replayed); then the
+    // tiles of the last level
+    auto persistent = [&](bool with_particles) -> cudaError_t {
+      for (auto& g : groups) {
+        int stuck = -1;
+        for (size_t c = 0; c < g.handles.size(); ++c)
+          if (g.handles[c] == g_stuck_handle) stuck = (int)c;
+        cudaError_t el;
+        if (g.f64) {
+          PersistentBatch<double> A{};
+          fill_persistent(A, dev, g, d_part, with_particles, stuck);
+          el = launch_lattice_persistent_f64(A, g.grid, g.held, bs);
+        } else {
+          PersistentBatch<float> A{};
+          fill_persistent(A, dev, g, d_part, with_particles, stuck);
+          el = launch_lattice_persistent_f32(A, g.grid, g.storage, g.held, bs);
+        }
+        if (el != cudaSuccess) return el;
+      }
+      if (with_particles && any_ellipse)
+        return launch_particle_band_ellipse_batch(d_part, d_items, nitems, 0,
+                                                  &reinterpret_cast<const BatchCtl*>(dev + groups[0].ctl_off)->k, bs);
+      return cudaSuccess;
+    };
+    e = launch_particle_step_batch(d_part, d_items, nitems, 0, any_ellipse, bs);
+    const int reps = nsteps - 1;
+    bool captured = false;
+    if (e == cudaSuccess && reps >= 2) {
+      captured = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (!captured) cudaGetLastError();  // a stream that cannot be captured (the legacy default stream)
+    }
+    if (captured) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      const cudaError_t eb = persistent(true);
+      e = cudaStreamEndCapture(bs, &graph);
+      if (e == cudaSuccess) e = eb;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, bs);
+      if (exec) cudaGraphExecDestroy(exec);  // (freed once its launches are done)
+      if (graph) cudaGraphDestroy(graph);
+    } else {
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = persistent(true);
+    }
+    if (e == cudaSuccess) e = persistent(false);
   }
   const cudaError_t ef = cudaFreeAsync(dev, bs);
   if (e != cudaSuccess) return bad(0, cuda_fail(h0, e, "batch kernels"));
@@ -959,6 +1137,13 @@ extern "C" {
 
 vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed) {
   return step_batch_impl(hs, n, nsteps, failed, nullptr, nullptr, nullptr);
+}
+
+vlb_status vlb_debug_batch_wait(int64_t wait_ns, int32_t stuck_handle) {
+  if (stuck_handle < -1) return fail(nullptr, VLB_EINVAL, "vlb_debug_batch_wait: stuck_handle < -1");
+  g_wait_ns = wait_ns > 0 ? (long long)wait_ns : 1000000000ll;
+  g_stuck_handle = stuck_handle;
+  return VLB_OK;
 }
 
 vlb_status vlb_synchronize(vlb_handle* h) {

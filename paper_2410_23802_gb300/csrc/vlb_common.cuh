@@ -52,6 +52,7 @@ enum : unsigned {
   ERR_TOO_FAST = 32u,
   ERR_NAN = 64u,
   ERR_BAND = 128u,  // a band cell whose table entry is not of the current level
+  ERR_TIMEOUT = 256u,  // a bounded device-side wait of a persistent launch ran out
 };
 
 // Band-table stamps run 1 .. 2^29 - 1 and then start again at 1 (0: none
@@ -90,9 +91,10 @@ struct ParticleArrays {
   unsigned long long* mes; // [n][3][2] F_MES,x + contact x, F_MES,y + contact y, T_MES as fixed point (mes_add)
   int* nbr_count;          // contact partners per particle
   int* nbr;                // [n][NBR_CAP], unordered (sorted where used)
-  int* fixed_T;            // [n] 1: the particle is held at its temperature T0 (reading R11)
+  int* fixed_T;            // [n] held at T0: 1 over the covered part (reading R11), 2 whole cells (R11b)
   double* pk;              // [n][8] constants: 1/M, 1/I, M_in, I_in, body force factor, wall factor
   RasterRec* rec;          // [n] raster records of the current level
+  int* pending;            // [n] tiles of its range still to finish the level (set by the particle step)
   int2* band;              // [n][bw][bw] band tables: (class | stamp << 2, area bits) of the cells of
                            // each disk's box, bw = 2 band_off + 1, centred on the record's cell
 };

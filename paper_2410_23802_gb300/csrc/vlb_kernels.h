@@ -49,6 +49,17 @@ cudaError_t launch_lattice_f32(int mode, const LatticeConst<float>& K, const Ste
 cudaError_t launch_lattice_f64(int mode, const LatticeConst<double>& K, const StepBuffers& B,
                                const ParticleArrays& P, const TileLists& TL, cudaStream_t st);
 
+// Level s of one case with the particle steps of level s + 1 folded in (a
+// case without ellipses): TL the level's lists (read, then cleared), PC the
+// particle constants with the stamp of level s + 1, TLn the cleared list
+// buffer the particle steps append to.
+cudaError_t launch_lattice_folded_f32(const LatticeConst<float>& K, const StepBuffers& B, const ParticleArrays& P,
+                                      const TileLists& TL, const ParticleConst& PC, const TileLists& TLn,
+                                      cudaStream_t st, int storage);
+cudaError_t launch_lattice_folded_f64(const LatticeConst<double>& K, const StepBuffers& B, const ParticleArrays& P,
+                                      const TileLists& TL, const ParticleConst& PC, const TileLists& TLn,
+                                      cudaStream_t st);
+
 // Ownership dump of the current level (inspection of the integer raster).
 cudaError_t launch_raster_dump_f32(const LatticeConst<float>& K, const ParticleArrays& P,
                                    const TileLists& TL, unsigned char* count, int* owner,
@@ -77,6 +88,44 @@ cudaError_t launch_lattice_batch_f32(const BatchLattice<float>* cases, const int
                                      int storage, bool held, cudaStream_t st);
 cudaError_t launch_lattice_batch_f64(const BatchLattice<double>* cases, const int* tile_case, int ntiles, int k,
                                      bool held, cudaStream_t st);
+
+// The persistent form of a batched step: one launch of a grid the size of the
+// GPU's resident capacity per level.  Its CTAs take work chunks in order from
+// a device counter: first the lattice tiles of level k -> k + 1 of every case
+// (one tile each), then, with with_particles, the particle steps of the next
+// level (one particle per warp), each after a bounded wait for the last tile
+// of its own case.  Every chunk that a waiting warp depends on was taken
+// earlier by a CTA that is running and never waits, so the waits end.  The
+// last CTA to leave resets the counters and advances k.
+struct BatchCtl {
+  int next;    // next work chunk
+  int exited;  // CTAs that have left this launch
+  int k;       // level step of the call that this launch's tiles compute
+  int pad;
+};
+template <class C>
+struct PersistentBatch {
+  const BatchLattice<C>* cases;  // the launch's cases
+  const int* tile_case;          // case of every tile, tiles of one case together
+  const BatchParticles* pcases;  // particle descriptors of the call's handles
+  const int* case_handle;        // handle index of every case of the launch
+  const int2* pitems;            // (case of the launch, particle) of its particles
+  BatchCtl* ctl;
+  int* done;                     // tiles finished per case in this launch
+  int ntiles, npitems, ncases;
+  int with_particles;            // 1: the particle steps of level k + 1 follow
+  int stuck_case;                // test hook: this case's wait never ends (-1: none)
+  long long wait_ns;             // limit of one wait (ns); past it ERR_TIMEOUT
+};
+// CTAs of one persistent launch (resident capacity of the variant on `device`).
+int persistent_grid(int device, bool f64, int storage, bool held);
+cudaError_t launch_lattice_persistent_f32(const PersistentBatch<float>& A, int grid, int storage, bool held,
+                                          cudaStream_t st);
+cudaError_t launch_lattice_persistent_f64(const PersistentBatch<double>& A, int grid, bool held, cudaStream_t st);
+// The band pass of the batch's ellipses for step k, or for step *kdev when
+// kdev is given (the level a persistent launch has just advanced to).
+cudaError_t launch_particle_band_ellipse_batch(const BatchParticles* cases, const int2* items, int nitems, int k,
+                                               const int* kdev, cudaStream_t st);
 
 // FP64 audits: out[0] = sum f, out[1] = sum eps, out[2] = sum g (block partials
 // in scratch[3 * nblocks], summed in block order).

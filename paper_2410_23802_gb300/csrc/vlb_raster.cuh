@@ -74,7 +74,7 @@ struct PartTile : EllPart<C> {
   C lam_s, T0;
   int id;                 // particle id
   int ci, cj;             // cell of the centre (band table origin)
-  int fixed;              // held at its temperature T0 (reading R11)
+  int fixed;              // held at T0: 1 covered part (reading R11), 2 whole cells (R11b)
   int rx, ry;             // first tile of the particle's range
 };
 

@@ -340,7 +340,10 @@ vlb_status vlb_serve_poll(vlb_server* s, int32_t* nqueued, int32_t* nactive, int
   std::vector<ServeCase*> admitted;
   while (!s->queue.empty()) {
     ServeCase* c = s->queue.front();
-    if (s->sp.max_active > 0 && (int)(s->active.size() + admitted.size()) >= s->sp.max_active) break;
+    // (cases whose read-back is still in flight are resident too)
+    if (s->sp.max_active > 0 &&
+        (int)(s->active.size() + s->draining.size() + admitted.size()) >= s->sp.max_active)
+      break;
     if (s->used + c->bytes > s->budget) break;
     s->queue.pop_front();
     s->used += c->bytes;
@@ -359,10 +362,8 @@ vlb_status vlb_serve_poll(vlb_server* s, int32_t* nqueued, int32_t* nactive, int
   }
   for (ServeCase* c : admitted) keep.push_back(c);
   s->active.swap(keep);
-  // 4. nothing left to queue: wait for the read-backs instead of spinning
-  if (s->active.empty() && (s->queue.empty() || admitted.empty()) && !s->draining.empty() &&
-      (s->queue.empty() || s->used + s->queue.front()->bytes > s->budget))
-    complete_draining(s, true);
+  // 4. no round to run: wait for the read-backs instead of spinning
+  if (s->active.empty() && !s->draining.empty()) complete_draining(s, true);
   int32_t done = 0;
   for (auto& kv : s->cases)
     if (kv.second->state == VLB_CASE_DONE || kv.second->state == VLB_CASE_FAILED) ++done;

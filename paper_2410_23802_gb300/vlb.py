@@ -87,6 +87,7 @@ def _load():
         "vlb_step": (ctypes.c_int, [h, ctypes.c_int32]),
         "vlb_insert_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
         "vlb_step_batch": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
+        "vlb_debug_batch_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32]),
         "vlb_synchronize": (ctypes.c_int, [h]),
         "vlb_get_step": (ctypes.c_int, [h, P(ctypes.c_int64)]),
         "vlb_get_fields": (ctypes.c_int, [h, ctypes.c_uint32, d, d, d, d, d]),
@@ -216,6 +217,12 @@ def vlb_step_batch(handles, nsteps: int = 1):
     _check(st, handles[failed.value] if failed.value >= 0 else None)
 
 
+def vlb_debug_batch_wait(wait_ns: int = 0, stuck_handle: int = -1) -> None:
+    """Test hook: the limit of vlb_step_batch's device-side waits (0: one second) and a handle position whose
+    waits never end (-1: none)."""
+    _check(_lib.vlb_debug_batch_wait(int(wait_ns), int(stuck_handle)), None)
+
+
 def vlb_synchronize(h):
     _check(_lib.vlb_synchronize(h), h)
 
@@ -320,7 +327,8 @@ def vlb_get_contact_pairs(h) -> np.ndarray:
 
 
 def vlb_set_fixed_temperature(h, held, first: int = 0) -> None:
-    """Hold particles first .. first + len(held) - 1 at their temperature T0 where held is true."""
+    """Hold particles first .. first + len(held) - 1 at their temperature T0: held 1 (reading R11, the covered
+    part of each cell), 2 (reading R11b, every owned cell whole), 0 conduct."""
     a = np.ascontiguousarray(np.asarray(held, dtype=np.int32))
     _check(_lib.vlb_set_fixed_temperature(h, int(first), int(a.size), _ptr(a, ctypes.c_int32)), h)
 

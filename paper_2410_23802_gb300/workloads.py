@@ -17,7 +17,8 @@ cavity    cold disks in a square cavity (Sec. 3.5): side L, N disks of D = 16
           bottom wall T = 1, top wall T = 0, adiabatic sides, fluid T = 1,
           particles T = 0, R_lambda = 5 (or per-particle log-uniform in
           [0.1, 10]), R_cv = 2, Pr = 0.71, tau_f = 0.8, sigma_0 = sigma_e =
-          sigma_eps = 1 (Sec. 3.5), g = 1e-5, beta from Gr = 100 on D.
+          sigma_eps = 1 (Sec. 3.5), g = 1e-5, beta from Gr = 100 on the
+          cavity height.
 """
 from __future__ import annotations
 
@@ -115,11 +116,12 @@ def channel(precision: str = "fp64") -> Case:
     return Case("channel 100x400, 1 disk D=20", params, [50.0], [300.0], [10.0], [0.0])
 
 
-def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision: str = "fp32") -> Case:
+def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision: str = "fp32", hold: int = 1) -> Case:
     """Sedimentation of a disk held at T_c = 0 in a long channel (the paper's
     Sec. 3.3 case, Table 4): D = 20 lu, width 4D, the disk starting D/2
     left of the centreline (x = 1.5 D), rho_r = 1.00232, Re = 40.5, Pr = 0.7,
-    Grashof number gr, tau_f = 0.53, R_lambda = R_cv = 1; fluid and walls at
+    Grashof number gr, tau_f = 0.53, R_lambda = R_cv = 1 (hold: 1 reading R11, 2
+    reading R11b of how the particle is held); fluid and walls at
     T_h = 1 (T_ref = T_h).  The channel length is not given (length_d
     diameters; the disk starts 10 D below the top)."""
     D = 20.0
@@ -132,7 +134,7 @@ def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision
                   T_fluid_init=1.0, thermal_wall=(1, 1, 1, 1), wall_T=(1.0, 1.0, 1.0, 1.0),
                   thermal_rates_mode=0, precision=precision)
     return Case(f"fixed-temperature sedimentation {nx}x{ny}, Gr={gr:g}", params, [1.5 * D], [ny - 10.0 * D],
-                [D / 2.0], [0.0], None, [1])
+                [D / 2.0], [0.0], None, [hold])
 
 
 def ellipse_sedimentation(length_w: float = 30.0, theta0: float = math.pi / 4, x_offset: float = 0.0,
@@ -188,8 +190,12 @@ def cavity(side: int = 2048, n: int = 2048, diameter: float = 16.0, seed: int = 
     nu = (0.8 - 0.5) / 3.0
     g = 1e-5
     xs, ys = place_disks(side, side, n, diameter, seed, gap=gap)
+    # beta from Gr = 100 on the cavity height (reading R9): with the held
+    # bottom and top walls the cavity is a Rayleigh-Benard cell, and Gr on
+    # the disk diameter would make it one at Ra ~ 1e11, which leaves the
+    # low-Mach range within the configuration's 20,000 steps
     params = dict(nx=side, ny=side, tau_f=0.8, prandtl=0.71, rho_ratio=1.2, cv_ratio=2.0, k_ratio_default=5.0,
-                  gravity=(0.0, -g), beta=gr_beta(100.0, nu, g, 1.0, diameter), T_ref=1.0, T_fluid_init=1.0,
+                  gravity=(0.0, -g), beta=gr_beta(100.0, nu, g, 1.0, float(side)), T_ref=1.0, T_fluid_init=1.0,
                   thermal_wall=(0, 0, 1, 1), wall_T=(0.0, 0.0, 1.0, 0.0), thermal_rates_mode=1,
                   precision=precision)
     k = None

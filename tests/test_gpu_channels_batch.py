@@ -4,8 +4,9 @@ single-disk channels, widths 64..256, each 4 widths long.
 * Batching changes nothing: every case stepped in the batch is bit for bit
   the case stepped alone with vlb_step (fields, particle state, step count),
   also in a batch that mixes FP32, FP64, FP16 and BF16 storage, held
-  particles, many disks in contact range and none (one launch of each
-  lattice kernel variant per step), and with single steps between calls.
+  particles, many disks in contact range, an ellipse in a channel with an
+  open bottom and none (one persistent launch of each lattice kernel variant
+  per step), and with single steps between calls.
 * The batch against the FP64 oracle: the narrowest, the widest and one
   middle channel of the 256-case batch, element by element (FP32 bar: 1e-5
   relative L2 on rho, u, T; 1e-4 on the particle).
@@ -43,8 +44,9 @@ def _mixed_cases():
     cav = W.cavity(side=96, n=6, seed=2)
     empty = dataclasses.replace(W.channels(n=1, seed=9)[0], x=[], y=[], radius=[], T0=[])
     held = dataclasses.replace(ch[5], fixed_T=[1])
+    ell = W.ellipse_sedimentation(length_w=5.0)
     return [(ch[0], "fp32"), (ch[1], "fp32"), (ch[2], "fp64"), (ch[3], "fp16"), (ch[4], "bf16"),
-            (held, "fp32"), (cav, "fp32"), (empty, "fp32"), (cav, "fp64")]
+            (held, "fp32"), (cav, "fp32"), (empty, "fp32"), (cav, "fp64"), (ell, "fp32")]
 
 
 def test_batch_equals_alone():

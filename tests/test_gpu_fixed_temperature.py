@@ -1,6 +1,8 @@
-"""Particles held at their temperature (reading R11, the held-temperature
-sedimentation case of Sec. 3.3): the CUDA path against the FP64 oracle on a small cavity
-where some disks are held and the others conduct, in FP32 and FP64."""
+"""Particles held at their temperature (readings R11 and R11b of the
+held-temperature sedimentation case of Sec. 3.3): the CUDA path against the
+FP64 oracle on a small cavity where some disks are held (over the covered
+part of each cell, or over every owned cell whole) and the others conduct,
+in FP32 and FP64."""
 import dataclasses
 
 import pytest
@@ -11,15 +13,16 @@ from paper_2410_23802_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _case():
+def _case(mode=1):
     base = W.cavity(side=128, n=12, seed=7)
-    held = [1 if k % 2 == 0 else 0 for k in range(len(base.x))]
+    held = [mode if k % 2 == 0 else 0 for k in range(len(base.x))]
     return dataclasses.replace(base, fixed_T=held)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp64", 1e-9)])
-def test_held_particles_match_oracle(precision, tol):
-    case = _case()
+def test_held_particles_match_oracle(precision, tol, mode):
+    case = _case(mode)
     ref = _oracle_snapshots(case, 3)
     gpu = _gpu_snapshots(case, 3, precision)
     _compare(gpu, ref, tol, 1e-4, 1e-4)

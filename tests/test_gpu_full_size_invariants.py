@@ -60,3 +60,22 @@ def test_closed_box_mass_of_the_bench_case():
         m1 = lat.audit()[0]
     print(f"mass {m0:.10e} -> {m1:.10e}, relative drift {abs(m1 / m0 - 1):.2e}")
     assert abs(m1 / m0 - 1) < 1e-8
+
+
+def test_bench_cavity_runs_its_20000_steps():
+    """The 2048^2 cavity with 2048 disks for the configuration's 20,000 steps
+    (beta from Gr = 100 on the cavity height, reading R9): no device flag
+    (no NaN, no disk faster than 0.5 lu per step, none out of the domain),
+    the disks settled lower, mass kept."""
+    case = W.cavity(side=2048, n=2048)
+    with gpu_lattice(case, precision="fp32") as lat:
+        m0 = lat.audit()[0]
+        y0 = np.array(case.y)
+        for _ in range(20):
+            lat.step(1000)  # raises on a device flag
+        ps = lat.particles()
+        m1 = lat.audit()[0]
+    speed = np.hypot(ps["ux"], ps["uy"])
+    print(f"20000 steps: largest disk speed {speed.max():.3e}, mean settling {np.mean(y0 - ps['y']):.1f} lu")
+    assert speed.max() < 0.5 and np.mean(y0 - ps["y"]) > 0.5
+    assert abs(m1 - m0) / m0 < 1e-7

@@ -139,11 +139,11 @@ def test_paper_cavity_balance_temperature():
     assert abs(teq - gold["T_eq"]) < 5e-5
 
 
-def _fixed_T_sim(ux=0.0, T_p=0.0, beta=0.0, walls=(1, 1, 1, 1), wall_T=1.0):
+def _fixed_T_sim(ux=0.0, T_p=0.0, beta=0.0, walls=(1, 1, 1, 1), wall_T=1.0, mode=1):
     p = V.Params(nx=48, ny=48, tau_f=0.8, prandtl=0.7, rho_ratio=1.0, cv_ratio=1.0, k_ratio_default=1.0,
                  gravity=(0.0, -1e-5), beta=beta, T_ref=1.0, T_fluid_init=1.0, thermal_wall=walls,
                  wall_T=(wall_T,) * 4)
-    return V.Simulation(p, [20.3], [24.6], [7.0], [T_p], ux=[ux], fixed_T=[True])
+    return V.Simulation(p, [20.3], [24.6], [7.0], [T_p], ux=[ux], fixed_T=[mode])
 
 
 def test_fixed_temperature_particle_interior_stays_at_its_temperature():
@@ -167,3 +167,36 @@ def test_fixed_temperature_particle_at_fluid_temperature_changes_nothing():
     sim = _fixed_T_sim(ux=0.02, T_p=1.0)
     sim.step(60)
     assert np.abs(sim.T - 1.0).max() < 1e-12
+
+
+def test_whole_cell_hold_sets_every_owned_cell():
+    """Reading R11b: every cell the held particle owns, interface cells
+    included, takes the equilibrium at T_p whole, so with R_cv = 1 its T is
+    T_p exactly there; under reading R11 the interface cells keep part of
+    the warmer fluid and lie strictly between T_p and the walls."""
+    T = {}
+    for mode in (1, 2):
+        sim = _fixed_T_sim(T_p=0.25, mode=mode)
+        sim.step(30)
+        T[mode] = sim.T.copy()
+        owned, partial = sim.ras.count > 0, (sim.ras.count > 0) & (sim.ras.fs < 1.0)
+    assert partial.sum() > 20
+    assert np.abs(T[2][owned] - 0.25).max() < 1e-13
+    assert (T[1][partial] > 0.25 + 1e-6).all()
+    assert np.abs(T[1][owned & ~partial] - 0.25).max() < 1e-13
+
+
+def test_whole_cell_holds_of_two_owners_share_the_cell():
+    """Reading R11b where two held particles own one cell: the cell takes
+    their mean equilibrium (weights summing above 1 are scaled to 1), so
+    with R_cv = 1 it sits at the mean of their temperatures; a cell owned by
+    one of them only is at that particle's temperature."""
+    p = V.Params(nx=40, ny=30, tau_f=0.8, prandtl=0.7, rho_ratio=1.0, cv_ratio=1.0, k_ratio_default=1.0,
+                 gravity=(0.0, 0.0), beta=0.0, T_ref=1.0, T_fluid_init=1.0)
+    sim = V.Simulation(p, [13.6, 26.0], [15.2, 15.2], [6.1, 6.1], [0.0, 1.0], fixed_T=[2, 2])
+    sim.step(1)
+    shared = sim.ras.count == 2
+    only = [(sim.ras.count == 1) & (sim.ras.owner[:, :, 0] == k) for k in (0, 1)]
+    assert shared.sum() >= 2
+    assert np.abs(sim.T[shared] - 0.5).max() < 1e-13
+    assert np.abs(sim.T[only[0]]).max() < 1e-13 and np.abs(sim.T[only[1]] - 1.0).max() < 1e-13
