@@ -294,7 +294,7 @@ static double min_image(double d, int L, int periodic) {
 static size_t particle_block_bytes(size_t capn) {
   return 16 * a256(capn * sizeof(double)) + a256(capn * sizeof(int4)) + a256(capn * sizeof(int)) +
          a256(capn * NBR_CAP * sizeof(int)) + a256(capn * sizeof(int)) + a256(capn * 8 * sizeof(double)) +
-         a256(capn * sizeof(int)) + a256(capn * sizeof(RasterRec));
+         a256(capn * sizeof(RasterRec));
 }
 static int band_offset(double rmax) { return (int)std::ceil(rmax) + 2; }
 constexpr int AUDIT_BLOCKS = 608;  // 4 x 152 SMs
@@ -395,7 +395,6 @@ vlb_status vlb_create_in(const vlb_params* pp, const vlb_handle_alloc* alloc, vl
     h->P.nbr = reinterpret_cast<int*>(b); b += a256(capn * NBR_CAP * sizeof(int));
     h->P.fixed_T = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.pk = reinterpret_cast<double*>(b); b += a256(capn * 8 * sizeof(double));
-    h->P.pending = reinterpret_cast<int*>(b); b += a256(capn * sizeof(int));
     h->P.rec = reinterpret_cast<RasterRec*>(b);
   }
   cudaMemsetAsync(h->pbase, 0, pbytes, h->stream);
@@ -666,73 +665,6 @@ static vlb_status step_once(vlb_handle* h) {
   return VLB_OK;
 }
 
-// Steps with the particle steps folded into the lattice launches (build
-// option VLB_FOLD_PARTICLES, on by default; cases without ellipses, whose
-// FP64 band pass keeps a kernel of its own): the particle step of level 0,
-// nsteps - 1 launches of lattice_folded_kernel (level s and the particle steps
-// of level s + 1), the last level's lattice_kernel.  The level buffers, list
-// buffers and stamps advance as nsteps calls of step_once would advance them,
-// so the two forms give the same bits and may alternate.
-#ifndef VLB_FOLD_PARTICLES
-#define VLB_FOLD_PARTICLES 1
-#endif
-constexpr bool kFoldParticles = VLB_FOLD_PARTICLES != 0;
-
-static vlb_status steps_folded(vlb_handle* h, int nsteps) {
-  int nl = 1 - h->tl;
-  next_band_stamp(h);
-  CK(h, launch_particle_step(h->PC, h->P, h->TL[nl], h->err_dev, h->stream));
-  // the buffer the particle steps of level 1 append to still holds the lists
-  // of the level before this call
-  CK(h, cudaMemsetAsync(h->TL[1 - nl].count, 0, (size_t)h->ntx * h->nty * sizeof(int), h->stream));
-  for (int k = 0; k + 1 < nsteps; ++k) {
-    StepBuffers B;
-    B.src = h->pop[h->cur];
-    B.dst = h->pop[1 - h->cur];
-    B.s_src = h->spl[h->cur];
-    B.s_dst = h->spl[1 - h->cur];
-    B.macro = h->macro;
-    B.err = h->err_dev;
-    TileLists TL = h->TL[nl];
-    TL.next_count = nullptr;  // read, then cleared tile by tile
-    TileLists TLn = h->TL[1 - nl];
-    TLn.next_count = nullptr;
-    ParticleConst PC = h->PC;
-    PC.band_stamp = band_stamp_after(h->PC.band_stamp, 1);
-    const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
-    if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
-    cudaError_t e = h->p.precision == VLB_FP64
-                        ? launch_lattice_folded_f64(h->K64, B, h->P, TL, PC, TLn, h->stream)
-                        : launch_lattice_folded_f32(h->K32, B, h->P, TL, PC, TLn, h->stream, h->storage);
-    if (e != cudaSuccess) return cuda_fail(h, e, "lattice kernel");
-    if (rec) {
-      CK(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
-      h->ev_used += 2;
-    }
-    h->tl = nl;
-    h->cur = 1 - h->cur;
-    ++h->step;
-    h->macros_valid = false;
-    next_band_stamp(h);  // the stamp of the level the folded particle steps made
-    nl = 1 - nl;
-  }
-  // the last level: lattice_kernel, which clears the other list buffer for
-  // the next call's first particle step
-  const bool rec = h->prof && h->ev_used + 2 <= h->ev_cap;
-  if (rec) CK(h, cudaEventRecord(h->ev[h->ev_used], h->stream));
-  vlb_status s = launch_lattice(h, MODE_STEP, h->cur, 1 - h->cur, nl);
-  if (s != VLB_OK) return s;
-  if (rec) {
-    CK(h, cudaEventRecord(h->ev[h->ev_used + 1], h->stream));
-    h->ev_used += 2;
-  }
-  h->tl = nl;
-  h->cur = 1 - h->cur;
-  ++h->step;
-  h->macros_valid = false;
-  return VLB_OK;
-}
-
 vlb_status vlb_insert_particles(vlb_handle* h, int32_t n, const double* xy, const double* radius, const double* T0,
                                 const double* k_ratio, const double* uv, const double* omega) {
   if (!h) return VLB_EINVAL;
@@ -803,12 +735,8 @@ vlb_status vlb_step(vlb_handle* h, int32_t nsteps) {
   vlb_status s = device_flags(h);
   if (s != VLB_OK) return s;
   if (!h->initialized && (s = initialize(h)) != VLB_OK) return s;
-  if (kFoldParticles && nsteps >= 2 && h->PC.any_ellipse == 0) {
-    if ((s = steps_folded(h, nsteps)) != VLB_OK) return s;
-  } else {
-    for (int k = 0; k < nsteps; ++k)
-      if ((s = step_once(h)) != VLB_OK) return s;
-  }
+  for (int k = 0; k < nsteps; ++k)
+    if ((s = step_once(h)) != VLB_OK) return s;
   CK(h, pull_flags(h));
   return VLB_OK;
 }

@@ -94,7 +94,6 @@ struct ParticleArrays {
   int* fixed_T;            // [n] held at T0: 1 over the covered part (reading R11), 2 whole cells (R11b)
   double* pk;              // [n][8] constants: 1/M, 1/I, M_in, I_in, body force factor, wall factor
   RasterRec* rec;          // [n] raster records of the current level
-  int* pending;            // [n] tiles of its range still to finish the level (set by the particle step)
   int2* band;              // [n][bw][bw] band tables: (class | stamp << 2, area bits) of the cells of
                            // each disk's box, bw = 2 band_off + 1, centred on the record's cell
 };

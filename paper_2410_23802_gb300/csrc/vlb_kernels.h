@@ -49,17 +49,6 @@ cudaError_t launch_lattice_f32(int mode, const LatticeConst<float>& K, const Ste
 cudaError_t launch_lattice_f64(int mode, const LatticeConst<double>& K, const StepBuffers& B,
                                const ParticleArrays& P, const TileLists& TL, cudaStream_t st);
 
-// Level s of one case with the particle steps of level s + 1 folded in (a
-// case without ellipses): TL the level's lists (read, then cleared), PC the
-// particle constants with the stamp of level s + 1, TLn the cleared list
-// buffer the particle steps append to.
-cudaError_t launch_lattice_folded_f32(const LatticeConst<float>& K, const StepBuffers& B, const ParticleArrays& P,
-                                      const TileLists& TL, const ParticleConst& PC, const TileLists& TLn,
-                                      cudaStream_t st, int storage);
-cudaError_t launch_lattice_folded_f64(const LatticeConst<double>& K, const StepBuffers& B, const ParticleArrays& P,
-                                      const TileLists& TL, const ParticleConst& PC, const TileLists& TLn,
-                                      cudaStream_t st);
-
 // Ownership dump of the current level (inspection of the integer raster).
 cudaError_t launch_raster_dump_f32(const LatticeConst<float>& K, const ParticleArrays& P,
                                    const TileLists& TL, unsigned char* count, int* owner,

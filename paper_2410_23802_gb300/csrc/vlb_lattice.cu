@@ -1,8 +1,6 @@
 // The single-case lattice kernels: the fused step (see vlb_lattice_body.cuh),
-// the same with the next level's particle steps folded in, the ownership dump
-// and the FP64 audits.
+// the ownership dump and the FP64 audits.
 #include "vlb_lattice_body.cuh"
-#include "vlb_particle_body.cuh"
 
 namespace vlb {
 
@@ -83,86 +81,6 @@ __global__ void audit_final_kernel(const double* scratch, int nblocks, double* o
   double s = 0.0;
   for (int b = 0; b < nblocks; ++b) s += scratch[3 * b + threadIdx.x];
   out[threadIdx.x] = s;
-}
-
-// The particle step of level s + 1 of particle p (one warp), in the CTA of
-// the last tile of its level-s range to finish.
-__device__ __forceinline__ void folded_particle(const ParticleConst& c, const ParticleArrays& P, const TileLists& TLn,
-                                             unsigned* err, int p, int* queue) {
-  const int lane = threadIdx.x & 31;
-  if (lane == 0) advance_one(c, P, p, err);
-  __syncwarp();
-  if (P.rb[p] == P.r[p]) band_one<false>(c, P, TLn, err, p, c.band_stamp, queue, lane);
-}
-
-// Level s of one case with the particle steps of level s + 1 folded in
-// (vlb_step of two or more steps of a case without ellipses).  Each CTA does
-// tile (x, y) as lattice_kernel<STEP> does, reading the level's tile list TL;
-// then, for each particle of that list, it counts the tile off the particle's
-// pending count (the tiles of its range, set by its previous particle step),
-// and the CTA that takes a count to zero runs that particle's step of level
-// s + 1 (PC: its stamp; TLn: the list buffer it appends to, cleared before).
-// The step reads the exchange sums, contact forces and partners that only
-// the tiles of its range add, and rewrites the record, band table and
-// position that only those tiles read, so it is ordered after all of them
-// and after nothing else; no CTA waits for another.  The tile's count in TL is
-// cleared once read (that buffer takes the particle steps of level s + 2 in
-// the next launch).  A tile-list overflow leaves a count above zero: that
-// particle does not move, and the overflow flag is raised.
-template <class S, class C, bool HOLD>
-__global__ void __launch_bounds__(TILE_X * TILE_Y, sizeof(C) == 4 ? VLB_LATTICE_MIN_BLOCKS : 1)
-lattice_folded_kernel(const LatticeConst<C> K, const StepBuffers B, const __grid_constant__ ParticleArrays P,
-                      const TileLists TL, const __grid_constant__ ParticleConst PC,
-                      const __grid_constant__ TileLists TLn) {
-  constexpr int NWARPS = TILE_X * TILE_Y / 32;
-  union Shared {
-    TileShared<C> tile;             // the tile's particles
-    int queue[NWARPS][BAND_QUEUE];  // band queues of the particle steps
-  };
-  __shared__ Shared sh;
-  __shared__ int s_ready[TILE_CAP];
-  __shared__ int s_nready;
-  const int tid = threadIdx.y * TILE_X + threadIdx.x;
-  if (tid == 0) s_nready = 0;  // (published by the barriers of a tile with particles)
-  C f[9], g[9], s_old;
-  pull_direct<S, C, MODE_STEP>(K, B, blockIdx.x, blockIdx.y, f, g, s_old);
-  const int np = cell_body<S, C, MODE_STEP, HOLD>(K, B, P, TL, blockIdx.x, blockIdx.y, f, g, s_old, sh.tile,
-                                                  K.band_stamp);
-  if (np == 0) return;  // the same for every thread
-  __syncthreads();      // every thread's sums of this tile are issued
-  if (tid < np) {
-    const int id = sh.tile.p[tid].id;
-    __threadfence();
-    if (atomicSub(P.pending + id, 1) == 1) s_ready[atomicAdd(&s_nready, 1)] = id;
-  }
-  if (tid == 0) TL.count[blockIdx.y * K.ntx + blockIdx.x] = 0;
-  __syncthreads();
-  const int nr = s_nready;
-  if (nr == 0) return;
-  __threadfence();
-  for (int r = tid >> 5; r < nr; r += NWARPS) folded_particle(PC, P, TLn, B.err, s_ready[r], sh.queue[tid >> 5]);
-}
-
-template <class S, class C>
-static cudaError_t launch_folded(const LatticeConst<C>& K, const StepBuffers& B, const ParticleArrays& P,
-                                 const TileLists& TL, const ParticleConst& PC, const TileLists& TLn, cudaStream_t st) {
-  dim3 grid(K.ntx, K.nty), block(TILE_X, TILE_Y);
-  if (K.any_held) lattice_folded_kernel<S, C, true><<<grid, block, 0, st>>>(K, B, P, TL, PC, TLn);
-  else lattice_folded_kernel<S, C, false><<<grid, block, 0, st>>>(K, B, P, TL, PC, TLn);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_lattice_folded_f32(const LatticeConst<float>& K, const StepBuffers& B, const ParticleArrays& P,
-                                      const TileLists& TL, const ParticleConst& PC, const TileLists& TLn,
-                                      cudaStream_t st, int storage) {
-  if (storage == STORE_F16) return launch_folded<__half, float>(K, B, P, TL, PC, TLn, st);
-  if (storage == STORE_BF16) return launch_folded<__nv_bfloat16, float>(K, B, P, TL, PC, TLn, st);
-  return launch_folded<float, float>(K, B, P, TL, PC, TLn, st);
-}
-cudaError_t launch_lattice_folded_f64(const LatticeConst<double>& K, const StepBuffers& B, const ParticleArrays& P,
-                                      const TileLists& TL, const ParticleConst& PC, const TileLists& TLn,
-                                      cudaStream_t st) {
-  return launch_folded<double, double>(K, B, P, TL, PC, TLn, st);
 }
 
 template <class S, class C>

@@ -89,14 +89,14 @@ __device__ __forceinline__ void advance_one(const ParticleConst& c, const Partic
   // momentum-exchange force and torque of the current level (Eq. 28) plus the
   // particle-particle contact forces of that level: the lattice kernel's
   // integer accumulators, read and cleared for the next level
+  // (read and cleared at the L2 with atomic exchanges, so that a particle
+  // step inside a lattice launch never reads an L1 line this SM loaded
+  // before other SMs added to the words)
   unsigned long long* acc = P.mes + 6 * (long long)p;
-  const ulonglong2 a0 = reinterpret_cast<const ulonglong2*>(acc)[0];
-  const ulonglong2 a1 = reinterpret_cast<const ulonglong2*>(acc)[1];
-  const ulonglong2 a2 = reinterpret_cast<const ulonglong2*>(acc)[2];
-  const double Fm_x = mes_value(a0.x, a0.y), Fm_y = mes_value(a1.x, a1.y), Tm = mes_value(a2.x, a2.y);
-  reinterpret_cast<ulonglong2*>(acc)[0] = make_ulonglong2(0ull, 0ull);
-  reinterpret_cast<ulonglong2*>(acc)[1] = make_ulonglong2(0ull, 0ull);
-  reinterpret_cast<ulonglong2*>(acc)[2] = make_ulonglong2(0ull, 0ull);
+  unsigned long long a[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) a[i] = atomicExch(acc + i, 0ull);
+  const double Fm_x = mes_value(a[0], a[1]), Fm_y = mes_value(a[2], a[3]), Tm = mes_value(a[4], a[5]);
   P.nbr_count[p] = 0;  // the lattice kernel of this step lists the next partners
   // wall contact forces: walls x-, x+, y-, y+ (none on open sides); an
   // ellipse meets a wall with its extent along the wall's normal (reading R13)
@@ -149,7 +149,6 @@ __device__ __forceinline__ void advance_one(const ParticleConst& c, const Partic
   write_record(P, p, Xn, Yn, R, Rb, uxn, uyn, omn, lam_s, T0);
   const int4 nr = tile_range(c, Xn, Yn, R);
   P.prange[p] = nr;
-  P.pending[p] = nr.z * nr.w;  // the tiles that will list it at the new level
   // (the band kernel that follows appends the particle to the tile lists)
 }
 
