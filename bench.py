@@ -343,8 +343,8 @@ def _channel_lattices(V, cases, streams):
 
 
 def _persistent_batches() -> bool:
-    from paper_2410_23802_gb300 import build as B
-    return "VLB_BATCH_PERSISTENT=0" not in B.tuned_defines()
+    from paper_2410_23802_gb300 import vlb as V
+    return V.vlb_get_batch_form() == V.VLB_BATCH_PERSISTENT
 
 
 def _batch_form() -> str:

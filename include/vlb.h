@@ -202,16 +202,20 @@ vlb_status vlb_insert_particles(vlb_handle* h, int32_t n, const double* xy, cons
 vlb_status vlb_step(vlb_handle* h, int32_t nsteps);
 
 /* nsteps time steps of each of n handles (independent cases of any sizes,
- * e.g. many small channels) with one persistent launch per step for all of
- * them (one per distinct precision / storage / held-path combination): a
- * grid of the GPU's resident capacity whose CTAs take, in order from a
- * device counter, the lattice tiles of every case and then the particle
- * steps of the next level, each particle after a bounded wait for the last
- * tile of its own case.  The launches of one step are the same every step:
- * they are captured once per call into a CUDA graph and replayed (plain
- * launches on the legacy default stream, which cannot be captured).  A wait
- * that runs out (VLB_ETIMEOUT on that handle) leaves the context usable.
- * Each handle advances exactly as vlb_step(h, nsteps) would,
+ * e.g. many small channels), in one of two forms (vlb_set_batch_form):
+ *   0  per step, one launch of the particle step over every particle of every
+ *      case and one lattice launch of one CTA per tile of any case (one per
+ *      distinct precision / storage / held-path combination);
+ *   1  per step, one persistent launch per such combination: a grid of the
+ *      GPU's resident capacity whose CTAs take, in order from a device
+ *      counter, the lattice tiles of every case and then the particle steps
+ *      of the next level, each particle after a bounded wait for the last
+ *      tile of its own case.  The launches of one step are the same every
+ *      step: they are captured once per call into a CUDA graph and replayed
+ *      (plain launches on the legacy default stream, which cannot be
+ *      captured).  A wait that runs out (VLB_ETIMEOUT on that handle) leaves
+ *      the context usable.
+ * Each handle advances exactly as vlb_step(h, nsteps) would, in either form,
  * bit for bit, and single steps and batch calls may alternate.  The work is
  * queued on hs[0]'s stream after the work already queued on every handle's
  * stream; every handle's stream then waits for it, so later calls on any
@@ -229,7 +233,14 @@ vlb_status vlb_step(vlb_handle* h, int32_t nsteps);
  * cases. */
 vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed);
 
-/* Test hook of the bounded waits of vlb_step_batch: wait_ns is the limit of
+/* The form of later vlb_step_batch calls and served rounds, process-wide:
+ * 0 or 1 as above.  The default is the build's (0 unless built with
+ * VLB_BATCH_PERSISTENT=1; on GB300 form 0 measured faster).  VLB_EINVAL for
+ * another value. */
+vlb_status vlb_set_batch_form(int32_t form);
+int32_t vlb_get_batch_form(void);
+
+/* Test hook of the bounded waits of vlb_step_batch (form 1): wait_ns is the limit of
  * each device-side wait (<= 0: the default, one second; a normal wait lasts
  * less than one lattice pass).  stuck_handle >= 0 names a position in the
  * handle array of later vlb_step_batch calls whose particle steps then wait

@@ -29,8 +29,9 @@ import sys
 from . import build as B
 
 # (tile height, CTAs per SM the registers are budgeted for (None: 1024 threads
-# per SM), persistent batched step (None: the default, on; 0: off))
-CANDIDATES = [(4, None, None), (2, None, None), (8, None, None), (4, 6, None), (4, None, 0), (8, None, 0)]
+# per SM), default form of the batched step (None: the build's default, one
+# CTA per tile; 1: persistent))
+CANDIDATES = [(4, None, None), (2, None, None), (8, None, None), (4, 6, None), (4, None, 1), (8, None, 1)]
 
 
 def candidates(workload: str) -> list[tuple]:

@@ -13,6 +13,7 @@
 //                      buffer 1 - b for the next step
 // The first step is preceded by the initial state (lattice INIT mode).
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cmath>
 #include <cstdio>
@@ -767,12 +768,13 @@ int g_stuck_handle = -1;
 
 size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 
-// The batched step in its persistent form (build option VLB_BATCH_PERSISTENT,
-// on by default), else one CTA per tile and a particle kernel per level.
+// The form of the batched step (vlb_set_batch_form): one CTA per tile and a
+// particle kernel per level, or the persistent launch.  The build option
+// VLB_BATCH_PERSISTENT sets the default (an autotuner candidate).
 #ifndef VLB_BATCH_PERSISTENT
-#define VLB_BATCH_PERSISTENT 1
+#define VLB_BATCH_PERSISTENT 0
 #endif
-constexpr bool kPersistent = VLB_BATCH_PERSISTENT != 0;
+std::atomic<int> g_batch_form{VLB_BATCH_PERSISTENT != 0 ? 1 : 0};
 
 template <class C>
 void fill_persistent(PersistentBatch<C>& A, unsigned char* dev, const BatchGroup& g, const BatchParticles* d_part,
@@ -857,6 +859,7 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
 
   // ---- descriptors -----------------------------------------------------------
   const int h0dev = hs[0]->device;
+  const bool persistent = g_batch_form.load() == 1;
   std::vector<BatchGroup> groups;
   std::vector<int2> items;
   for (int i = 0; i < n; ++i) {
@@ -889,7 +892,7 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
     bytes = align16(bytes + (g.f64 ? sizeof(BatchLattice<double>) : sizeof(BatchLattice<float>)) * g.handles.size());
     g.table_off = bytes;
     bytes = align16(bytes + sizeof(int) * nt);
-    if (kPersistent) {
+    if (persistent) {
       for (size_t c = 0; c < g.handles.size(); ++c)
         for (int k = 0; k < hs[g.handles[c]]->np; ++k) g.pitems.push_back(make_int2((int)c, k));
       g.pitems_off = bytes;
@@ -948,7 +951,7 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
       for (int t = 0; t < nt; ++t) table[tile0 + t] = (int)c;
       tile0 += nt;
     }
-    if (kPersistent) {
+    if (persistent) {
       if (!g.pitems.empty()) std::memcpy(hostp + g.pitems_off, g.pitems.data(), sizeof(int2) * g.pitems.size());
       int* ch = reinterpret_cast<int*>(hostp + g.chandle_off);
       for (size_t c = 0; c < g.handles.size(); ++c) ch[c] = g.handles[c];
@@ -972,7 +975,7 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
   const int nitems = (int)items.size();
   bool any_ellipse = false;
   for (int i = 0; i < n; ++i) any_ellipse |= hs[i]->PC.any_ellipse != 0;
-  if (!kPersistent) {
+  if (!persistent) {
     for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
       e = launch_particle_step_batch(d_part, d_items, nitems, k, any_ellipse, bs);
       for (auto& g : groups) {
@@ -1066,6 +1069,14 @@ extern "C" {
 vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int32_t* failed) {
   return step_batch_impl(hs, n, nsteps, failed, nullptr, nullptr, nullptr);
 }
+
+vlb_status vlb_set_batch_form(int32_t form) {
+  if (form != 0 && form != 1) return fail(nullptr, VLB_EINVAL, "vlb_set_batch_form: form must be 0 or 1");
+  g_batch_form.store(form);
+  return VLB_OK;
+}
+
+int32_t vlb_get_batch_form(void) { return g_batch_form.load(); }
 
 vlb_status vlb_debug_batch_wait(int64_t wait_ns, int32_t stuck_handle) {
   if (stuck_handle < -1) return fail(nullptr, VLB_EINVAL, "vlb_debug_batch_wait: stuck_handle < -1");

@@ -88,6 +88,8 @@ def _load():
         "vlb_insert_particles": (ctypes.c_int, [h, ctypes.c_int32, d, d, d, d, d, d]),
         "vlb_step_batch": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32)]),
         "vlb_debug_batch_wait": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32]),
+        "vlb_set_batch_form": (ctypes.c_int, [ctypes.c_int32]),
+        "vlb_get_batch_form": (ctypes.c_int32, []),
         "vlb_synchronize": (ctypes.c_int, [h]),
         "vlb_get_step": (ctypes.c_int, [h, P(ctypes.c_int64)]),
         "vlb_get_fields": (ctypes.c_int, [h, ctypes.c_uint32, d, d, d, d, d]),
@@ -215,6 +217,18 @@ def vlb_step_batch(handles, nsteps: int = 1):
     failed = ctypes.c_int32(-1)
     st = _lib.vlb_step_batch(hs, len(handles), int(nsteps), ctypes.byref(failed))
     _check(st, handles[failed.value] if failed.value >= 0 else None)
+
+
+VLB_BATCH_TILES, VLB_BATCH_PERSISTENT = 0, 1
+
+
+def vlb_set_batch_form(form: int) -> None:
+    """Form of later vlb_step_batch calls (process-wide): VLB_BATCH_TILES or VLB_BATCH_PERSISTENT."""
+    _check(_lib.vlb_set_batch_form(int(form)), None)
+
+
+def vlb_get_batch_form() -> int:
+    return int(_lib.vlb_get_batch_form())
 
 
 def vlb_debug_batch_wait(wait_ns: int = 0, stuck_handle: int = -1) -> None:

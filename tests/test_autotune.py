@@ -8,8 +8,8 @@ def test_tuner_records_the_fastest_shape(tmp_path):
     from paper_2410_23802_gb300 import autotune as A, build as B
     path = str(tmp_path / "tuned.json")
     built = []
-    times = {"tune_y4": 1.30, "tune_y2": 1.25, "tune_y8": 1.40, "tune_y4_b6": 1.35, "tune_y4_p0": 1.31,
-             "tune_y8_p0": 1.41}
+    times = {"tune_y4": 1.30, "tune_y2": 1.25, "tune_y8": 1.40, "tune_y4_b6": 1.35, "tune_y4_p1": 1.31,
+             "tune_y8_p1": 1.41}
 
     def fake_build(defines, out):
         built.append((tuple(defines), out))
@@ -20,7 +20,7 @@ def test_tuner_records_the_fastest_shape(tmp_path):
 
     rec = A.tune("channels", steps=7, path=path, build=fake_build, timer=fake_timer)
     assert len(built) == len(A.CANDIDATES) == len({b[1] for b in built})
-    assert ("VLB_TILE_Y=4", "VLB_BATCH_PERSISTENT=0") in [b[0] for b in built]
+    assert ("VLB_TILE_Y=4", "VLB_BATCH_PERSISTENT=1") in [b[0] for b in built]
     y2 = ["VLB_TILE_Y=2"]
     assert rec["channels"]["defines"] == y2 and rec["use"] == "channels"
     assert B.tuned_defines(path) == y2

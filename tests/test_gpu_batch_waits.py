@@ -1,5 +1,5 @@
-"""The persistent batched step (vlb_step_batch): its bounded waits and its
-plain-launch form.
+"""The persistent form of the batched step (vlb_step_batch, form 1): its
+bounded waits and its plain-launch form, and both forms on short calls.
 
 * A wait made to run out: with the test hook, the particle steps of the
   first case of a two-case batch wait for a tile count that is never
@@ -17,6 +17,15 @@ from helpers import gpu_lattice
 from paper_2410_23802_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def form():
+    """Sets the batched-step form for one test and restores the default."""
+    from paper_2410_23802_gb300 import vlb as V
+    old = V.vlb_get_batch_form()
+    yield V.vlb_set_batch_form
+    V.vlb_set_batch_form(old)
 
 
 def _state(lat):
@@ -45,8 +54,9 @@ def _cases():
     return [ch[0], ch[1], W.cavity(side=96, n=5, seed=4)]
 
 
-def test_wait_that_runs_out_reports_etimeout_and_leaves_the_context_usable():
+def test_wait_that_runs_out_reports_etimeout_and_leaves_the_context_usable(form):
     from paper_2410_23802_gb300 import vlb as V
+    form(V.VLB_BATCH_PERSISTENT)
     stuck, other = _cases()[:2]
     lats = [gpu_lattice(stuck), gpu_lattice(other)]
     try:
@@ -76,14 +86,18 @@ def test_wait_that_runs_out_reports_etimeout_and_leaves_the_context_usable():
         _same(g, _solo(c, 6))
 
 
-def test_debug_hook_rejects_a_bad_position():
+def test_bad_hook_position_and_form_are_refused():
     from paper_2410_23802_gb300 import vlb as V
     with pytest.raises(V.VlbError, match="EINVAL"):
         V.vlb_debug_batch_wait(0, -2)
+    with pytest.raises(V.VlbError, match="EINVAL"):
+        V.vlb_set_batch_form(2)
 
 
-def test_batch_on_the_legacy_default_stream():
+@pytest.mark.parametrize("which", [0, 1])
+def test_batch_on_the_legacy_default_stream(form, which):
     from paper_2410_23802_gb300 import vlb as V
+    form(which)
     cases = _cases()
     lats = [gpu_lattice(c) for c in cases]
     try:
@@ -98,9 +112,11 @@ def test_batch_on_the_legacy_default_stream():
         _same(g, _solo(c, 7))
 
 
+@pytest.mark.parametrize("which", [0, 1])
 @pytest.mark.parametrize("chunks", [(1,), (2,), (1, 1, 2, 1)])
-def test_short_calls_without_graph_replay(chunks):
+def test_short_calls_without_graph_replay(form, which, chunks):
     from paper_2410_23802_gb300 import vlb as V
+    form(which)
     cases = _cases()
     lats = [gpu_lattice(c) for c in cases]
     try:

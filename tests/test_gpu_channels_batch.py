@@ -49,7 +49,16 @@ def _mixed_cases():
             (held, "fp32"), (cav, "fp32"), (empty, "fp32"), (cav, "fp64"), (ell, "fp32")]
 
 
-def test_batch_equals_alone():
+@pytest.fixture(params=[0, 1], ids=["tiles", "persistent"])
+def batch_form(request):
+    from paper_2410_23802_gb300 import vlb as V
+    old = V.vlb_get_batch_form()
+    V.vlb_set_batch_form(request.param)
+    yield request.param
+    V.vlb_set_batch_form(old)
+
+
+def test_batch_equals_alone(batch_form):
     from paper_2410_23802_gb300 import vlb as V
     cases = _mixed_cases()
     chunks = (1, 17, 30, 0, 2)  # uneven calls, both parities; 50 steps in all
@@ -67,7 +76,7 @@ def test_batch_equals_alone():
             _same(g, _state(lat))
 
 
-def test_batch_then_single_steps_continue():
+def test_batch_then_single_steps_continue(batch_form):
     """vlb_step after vlb_step_batch (and the other way round) continues the
     same levels: buffer and list parities and band stamps carry over."""
     from paper_2410_23802_gb300 import vlb as V

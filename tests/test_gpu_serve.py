@@ -155,3 +155,36 @@ def test_unstable_case_fails_alone():
             assert np.array_equal(f[name], fs[name], equal_nan=True), name
         for name in ps:
             assert np.array_equal(p[name], ps[name]), name
+
+
+def test_served_results_against_the_oracle():
+    """Served cases against the FP64 oracle, not only against their solo runs:
+    two small cavities (FP32 and FP16 storage) admitted together with a third
+    case and stepped in shared rounds of uneven length.  FP32: rho, u, T
+    within 1e-5 relative L2, particles within 1e-4; FP16 storage: u and T
+    within 1e-3, particles within 1e-3."""
+    from helpers import oracle_sim, rel_l2
+    from paper_2410_23802_gb300 import vlb as V
+    a = W.cavity(side=96, n=4, seed=41, precision="fp32")
+    b = W.cavity(side=112, n=6, seed=43, precision="fp16")
+    c = W.cavity(side=128, n=8, seed=47, precision="fp32")
+    steps = {0: 60, 1: 50, 2: 37}
+    with V.Server(hbm_budget=1 << 30, steps_per_round=13) as srv:
+        ids = [_submit(srv, V, case, steps[k]) for k, case in enumerate((a, b, c))]
+        for _ in range(1000):
+            q, act, d = srv.poll()
+            if d == 3:
+                break
+        got = [srv.take(i) for i in ids[:2]]
+    for (case, n, tol, ptol), (f, p) in zip([(a, 60, 1e-5, 1e-4), (b, 50, 1e-3, 1e-3)], got):
+        sim = oracle_sim(case)
+        sim.step(n)
+        ref = sim.fields()
+        e_rho = rel_l2(f["rho"], ref["rho"])
+        e_u = rel_l2(np.stack([f["ux"], f["uy"]]), np.stack([ref["ux"], ref["uy"]]))
+        e_T = rel_l2(f["T"], ref["T"])
+        print(f"served {case.params['precision']}: rho {e_rho:.2e} u {e_u:.2e} T {e_T:.2e}")
+        assert e_u < tol and e_T < tol and (case.params["precision"] != "fp32" or e_rho < tol)
+        rp = sim.particle_state()
+        for k in ("x", "y", "ux", "uy"):
+            assert np.abs(p[k] - rp[k]).max() < ptol, k
