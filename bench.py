@@ -93,7 +93,7 @@ def _peaks():
 
 
 # the files the lattice kernel is compiled from
-LATTICE_SOURCES = ["vlb_common.cuh", "vlb_kernels.h", "vlb_lattice.cu", "vlb_raster.cuh"]
+LATTICE_SOURCES = ["vlb_common.cuh", "vlb_kernels.h", "vlb_lattice.cu", "vlb_lattice_body.cuh", "vlb_raster.cuh"]
 
 
 def _source_hash():
