@@ -364,7 +364,7 @@ const char* vlb_last_error(const vlb_handle* h);
 void vlb_destroy(vlb_handle* h);
 
 /* Device bytes that a handle of parameters p allocates for n particles of
- * the given radii (create, particles and first step; rows padded to 128 B,
+ * the given radii (create, particles and first step; rows padded to 32 B,
  * band tables sized by the largest radius).  VLB_EINVAL for inconsistent
  * parameters, as vlb_create would return it. */
 vlb_status vlb_device_bytes(const vlb_params* p, int32_t n, const double* radius, uint64_t* bytes);

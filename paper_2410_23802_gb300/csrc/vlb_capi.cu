@@ -264,7 +264,12 @@ static const char* params_error(const vlb_params& p) {
   return nullptr;
 }
 
-// Sizes and layout every handle of parameters p uses (rows padded to 128 B).
+// Sizes and layout every handle of parameters p uses.  Rows are padded to a
+// 32-byte sector, not to a 128-byte line: the L2 fetches whole lines from
+// DRAM, so the pad of a row padded to a line came in with its last cells
+// (about 9 B per cell update over 256 channels of widths 64..256, measured),
+// while with sector padding that line carries the next row's first cells,
+// which the tile at the start of the row has just used.
 struct Layout {
   int pitch, ntx, nty;
   long long plane;
@@ -274,7 +279,7 @@ static Layout layout_of(const vlb_params& p) {
   Layout L;
   L.esize = p.precision == VLB_FP64 ? 8 : 4;
   L.ssize = p.precision == VLB_FP64 ? 8 : (p.precision == VLB_FP32 ? 4 : 2);
-  const int align = 128 / (int)L.ssize;
+  const int align = 32 / (int)L.ssize;
   L.pitch = (p.nx + align - 1) / align * align;
   L.plane = (long long)L.pitch * p.ny;
   L.ntx = (p.nx + TILE_X - 1) / TILE_X;

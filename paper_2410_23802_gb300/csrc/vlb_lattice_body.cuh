@@ -12,7 +12,7 @@
 // S = 2 f_s + df_s/dt at level n+1.
 //
 // Layout in HBM: structure of arrays, one plane per direction, x fastest,
-// rows padded to 128 B.  f is stored as the deviation from the rest
+// rows padded to 32 B.  f is stored as the deviation from the rest
 // equilibrium w_i, g as the deviation from g^eq(T_fluid) (g_off), S in the
 // arithmetic type.  Populations ping-pong between two buffers.
 #pragma once

@@ -22,7 +22,8 @@ def test_footprint_orders():
     assert _bytes(V, nx=512) > b32
     assert _bytes(V, radius=[8.0] * 32) > b32
     assert _bytes(V, radius=[12.0] * 16) > b32          # larger band tables
-    assert _bytes(V, nx=250) == _bytes(V, nx=256)      # rows padded to 128 B
+    assert _bytes(V, nx=250) == _bytes(V, nx=256)      # rows padded to 32 B
+    assert _bytes(V, nx=248) < _bytes(V, nx=250)       # 248 needs no pad, 250 pads to 256
 
 
 def test_footprint_refuses_bad_parameters():
