@@ -1,13 +1,17 @@
-// Batched stepping of many cases (vlb_step_batch): the tiles of all cases of
-// one kernel variant in one grid, and the particle steps of all cases.
+// Batched stepping of many cases (vlb_step_batch), in two forms: per step a
+// particle kernel over the particles of every case and a lattice kernel of
+// one CTA per tile of any case (form 0); or one persistent launch per step
+// that takes the tiles and then the next level's particle steps from a
+// device counter, each particle step after a bounded wait for its case's
+// tiles (form 1).
 #include "vlb_lattice_body.cuh"
 #include "vlb_particle_body.cuh"
 
 namespace vlb {
 
 // Step k of a batch call (vlb_step_batch) over the tiles of many cases, one
-// CTA per tile as above: the tile's case descriptor is copied to shared
-// memory, then the single-case code runs on it.
+// CTA per tile: the tile's case descriptor is copied to shared memory, then
+// the single-case code (vlb_lattice_body.cuh) runs on it.
 template <class S, class C, bool HOLD>
 __global__ void __launch_bounds__(TILE_X * TILE_Y, sizeof(C) == 4 ? VLB_LATTICE_MIN_BLOCKS : 1)
 lattice_batch_kernel(const BatchLattice<C>* __restrict__ cases, const int* __restrict__ tile_case, int k) {
