@@ -495,11 +495,11 @@ def _latency_summary(lat_s, span, n, work):
             "cases_per_s": round(n / span, 2), "mlups": round(work / span / 1e6, 1)}
 
 
-def measure_served(V, local, n_cases, steps, budget_gb=2.0, round_steps=100, loads=(None, 1.2)):
+def measure_served(V, local, n_cases, steps, budget_gb=2.0, round_steps=100, loads=(None, 0.8, 1.2)):
     """A shortened seeded stream of the served configuration (cavities of
     side 2^U[6,10], 1-512 disks, half FP16 storage) through the server and
     through the plain path (one case after the other, FP32): all arriving at
-    once (saturation), and Poisson arrivals at 1.2 x the plain path's
+    once (saturation), and Poisson arrivals at 0.8 and 1.2 x the plain path's
     measured service rate.  Time to result = arrival to fields and particle
     state in host memory."""
     import torch
