@@ -235,6 +235,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2410_23802_gb300 import vlb as V
+    if args.batch_form is not None:
+        V.vlb_set_batch_form(args.batch_form)
 
     case = _make_case(args)
     cells = case.cells
@@ -552,6 +554,8 @@ def run_channels(args):
     if rank != 0:
         return
     torch.cuda.set_device(local)
+    if args.batch_form is not None:
+        V.vlb_set_batch_form(args.batch_form)
     cases = W.channels(n=args.cases, precision=args.precision)
     cells = sum(c.cells for c in cases)
     main_stream = torch.cuda.Stream()
@@ -621,7 +625,8 @@ def run_channels(args):
         "cases_per_s": round(len(cases) * args.steps / (batched_ms * 1e-3) / 5000.0, 2),
         "cases_per_s_note": "cases of 5000 steps each",
         "host_wall_mlups": round(cells * args.steps / host_s / 1e6, 1),
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": _batch_launches(args.steps),
+        "form": _batch_form(),
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -641,6 +646,9 @@ def run_serve(args):
     if rank != 0:
         return
     torch.cuda.set_device(local)
+    if args.batch_form is not None:
+        from paper_2410_23802_gb300 import vlb as _V
+        _V.vlb_set_batch_form(args.batch_form)
     r = measure_served(V, local, args.cases, args.serve_steps, budget_gb=args.budget_gb,
                        round_steps=args.round_steps, loads=(None, 0.8, 1.2))
     line = {
@@ -808,6 +816,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16, batched and served sub-records")
     ap.add_argument("--serve-cases", type=int, default=48, help="served sub-record: cases in the stream")
     ap.add_argument("--serve-case-steps", type=int, default=400, help="served sub-record: steps per case")
+    ap.add_argument("--batch-form", type=int, default=None, choices=[0, 1],
+                    help="form of vlb_step_batch (0 a CTA per tile, 1 persistent; default: the build's)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

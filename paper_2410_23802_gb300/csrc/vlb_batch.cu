@@ -144,10 +144,10 @@ __device__ bool wait_count(const int* count, int target, long long limit_ns) {
 
 // Particle item i of a persistent launch (one warp): the particle step of
 // level kn, after the last tile of its case (whose exchange sums, contact
-// partners and cleared list buffer it reads).  Out of line, so that its FP64
-// register needs stay apart from the tile code's.
+// partners and cleared list buffer it reads).  Inlined: as a call it cost
+// the tile path more (spills around the call) than its own FP64 code does.
 template <class C>
-__device__ __noinline__ void persistent_particle(const PersistentBatch<C>& A, int i, int kn, int* queue) {
+__device__ __forceinline__ void persistent_particle(const PersistentBatch<C>& A, int i, int kn, int* queue) {
   const int lane = threadIdx.x & 31;
   if (i >= A.npitems) return;
   const int2 it = A.pitems[i];
@@ -169,7 +169,7 @@ __device__ __noinline__ void persistent_particle(const PersistentBatch<C>& A, in
 // from the counter (one atomic round trip, which its first warp waits for)
 // only after its last one, so the trip is paid once per chunk.
 #ifndef VLB_BATCH_CHUNK
-#define VLB_BATCH_CHUNK 8
+#define VLB_BATCH_CHUNK 4
 #endif
 constexpr int BATCH_CHUNK = VLB_BATCH_CHUNK;
 
@@ -190,21 +190,34 @@ lattice_persistent_kernel(const __grid_constant__ PersistentBatch<C> A) {
   };
   __shared__ Shared sh;
   __shared__ BatchLattice<C> d;
-  __shared__ int s_item, s_end, s_case, s_k;
+  __shared__ int s_item, s_end, s_case, s_k, s_pend, s_pend_case;
   static_assert(sizeof(BatchLattice<C>) % 4 == 0, "descriptor copied as words");
   const int tid = threadIdx.y * TILE_X + threadIdx.x;
   const int tchunks = (A.ntiles + BATCH_CHUNK - 1) / BATCH_CHUNK;
   const int nitems = A.ntiles + (A.with_particles ? (A.npitems + NWARPS - 1) / NWARPS : 0);
-  if (tid == 0) {
+  // (thread 0) publish the finished tiles of one case: a fence, then one add
+  auto publish = [&]() {
+    if (s_pend > 0) {
+      __threadfence();
+      atomicAdd(A.done + s_pend_case, s_pend);
+      s_pend = 0;
+    }
+  };
+  auto take_chunk = [&]() {
     const int j = atomicAdd(&A.ctl->next, 1);
     s_item = j < tchunks ? j * BATCH_CHUNK : A.ntiles + (j - tchunks);
     s_end = j < tchunks ? min(A.ntiles, (j + 1) * BATCH_CHUNK) : s_item + 1;
+  };
+  if (tid == 0) {
+    take_chunk();
     s_case = -1;
     s_k = A.ctl->k;
+    s_pend = 0;
+    s_pend_case = -1;
   }
   __syncthreads();
+  int item = s_item, end = s_end;
   for (;;) {
-    const int item = s_item;
     if (item >= nitems) break;
     if (item < A.ntiles) {
       const int c = A.tile_case[item];
@@ -224,25 +237,31 @@ lattice_persistent_kernel(const __grid_constant__ PersistentBatch<C> A) {
       pull_direct<S, C, MODE_STEP>(d.K, B, tile_x, tile_y, f, g, s_old);
       cell_body<S, C, MODE_STEP, HOLD>(d.K, B, d.P, TL, tile_x, tile_y, f, g, s_old, sh.tile,
                                        band_stamp_after(d.stamp, s_k + 1));
-      __syncthreads();  // every thread's stores and sums of this tile are issued
+      __syncthreads();  // every thread's stores and sums of this tile are issued; sh and d are free
       if (tid == 0 && A.with_particles && d.K.np > 0) {
-        __threadfence();
-        atomicAdd(A.done + s_case, 1);
+        // counted now, published (fence + add) when the case changes or the
+        // chunk ends, so that a chunk of one case pays one fence
+        if (s_pend_case != s_case) {
+          publish();
+          s_pend_case = s_case;
+        }
+        ++s_pend;
       }
     } else {
       persistent_particle<C>(A, (item - A.ntiles) * NWARPS + (tid >> 5), s_k + 1, sh.queue[tid >> 5]);
+      __syncthreads();  // the band queues are free
     }
-    __syncthreads();
+    if (item + 1 < end) {  // the next tile of this chunk (every thread knows it)
+      ++item;
+      continue;
+    }
     if (tid == 0) {
-      int next = item + 1;
-      if (next >= s_end) {
-        const int j = atomicAdd(&A.ctl->next, 1);
-        next = j < tchunks ? j * BATCH_CHUNK : A.ntiles + (j - tchunks);
-        s_end = j < tchunks ? min(A.ntiles, (j + 1) * BATCH_CHUNK) : next + 1;
-      }
-      s_item = next;
+      publish();
+      take_chunk();
     }
     __syncthreads();
+    item = s_item;
+    end = s_end;
   }
   if (tid == 0) {
     __threadfence();
