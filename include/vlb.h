@@ -211,7 +211,8 @@ vlb_status vlb_step(vlb_handle* h, int32_t nsteps);
  *      counter, the lattice tiles of every case and then the particle steps
  *      of the next level, each particle after a bounded wait for the last
  *      tile of its own case.  The launches of one step are the same every
- *      step: they are captured once per call into a CUDA graph and replayed
+ *      step: up to 64 steps of them are captured into a CUDA graph (its
+ *      executable form kept per host thread and updated) and replayed
  *      (plain launches on the legacy default stream, which cannot be
  *      captured).  A wait that runs out (VLB_ETIMEOUT on that handle) leaves
  *      the context usable.
@@ -235,8 +236,9 @@ vlb_status vlb_step_batch(vlb_handle* const* hs, int32_t n, int32_t nsteps, int3
 
 /* The form of later vlb_step_batch calls and served rounds, process-wide:
  * 0 or 1 as above.  The default is the build's (0 unless built with
- * VLB_BATCH_PERSISTENT=1; on GB300 form 0 measured faster).  VLB_EINVAL for
- * another value. */
+ * VLB_BATCH_PERSISTENT=1; on GB300 the two forms measured equal on 256
+ * channels and form 0 faster in served rounds of a few small cases).
+ * VLB_EINVAL for another value. */
 vlb_status vlb_set_batch_form(int32_t form);
 int32_t vlb_get_batch_form(void);
 

@@ -781,6 +781,8 @@ size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 #define VLB_BATCH_PERSISTENT 0
 #endif
 std::atomic<int> g_batch_form{VLB_BATCH_PERSISTENT != 0 ? 1 : 0};
+// steps of the persistent form per captured CUDA graph
+constexpr int kGraphSteps = 64;
 
 template <class C>
 void fill_persistent(PersistentBatch<C>& A, unsigned char* dev, const BatchGroup& g, const BatchParticles* d_part,
@@ -1021,25 +1023,40 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
       return cudaSuccess;
     };
     e = launch_particle_step_batch(d_part, d_items, nitems, 0, any_ellipse, bs);
+    // the steps' launches are the same every step (the step index lives on
+    // the device): up to kGraphSteps of them are captured into one CUDA graph,
+    // replayed as often as it fits, and the rest launched plainly
     const int reps = nsteps - 1;
+    const int gsteps = std::min(reps, kGraphSteps);
     bool captured = false;
     if (e == cudaSuccess && reps >= 2) {
       captured = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       if (!captured) cudaGetLastError();  // a stream that cannot be captured (the legacy default stream)
     }
+    int done_reps = 0;
     if (captured) {
+      // the executable graph of the last call is kept (per host thread) and
+      // updated with this call's launches when they have the same shape, which
+      // costs far less than instantiating one per call
+      thread_local cudaGraphExec_t cached = nullptr;
       cudaGraph_t graph = nullptr;
-      cudaGraphExec_t exec = nullptr;
-      const cudaError_t eb = persistent(true);
+      cudaError_t eb = cudaSuccess;
+      for (int r = 0; r < gsteps && eb == cudaSuccess; ++r) eb = persistent(true);
       e = cudaStreamEndCapture(bs, &graph);
       if (e == cudaSuccess) e = eb;
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, bs);
-      if (exec) cudaGraphExecDestroy(exec);  // (freed once its launches are done)
+      if (e == cudaSuccess) {
+        cudaGraphExecUpdateResultInfo info;
+        if (!cached || cudaGraphExecUpdate(cached, graph, &info) != cudaSuccess) {
+          cudaGetLastError();
+          if (cached) cudaGraphExecDestroy(cached);  // (freed once its launches are done)
+          cached = nullptr;
+          e = cudaGraphInstantiate(&cached, graph, 0);
+        }
+      }
+      for (; done_reps + gsteps <= reps && e == cudaSuccess; done_reps += gsteps) e = cudaGraphLaunch(cached, bs);
       if (graph) cudaGraphDestroy(graph);
-    } else {
-      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = persistent(true);
     }
+    for (; done_reps < reps && e == cudaSuccess; ++done_reps) e = persistent(true);
     if (e == cudaSuccess) e = persistent(false);
   }
   const cudaError_t ef = cudaFreeAsync(dev, bs);
