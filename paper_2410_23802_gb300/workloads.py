@@ -116,7 +116,8 @@ def channel(precision: str = "fp64") -> Case:
     return Case("channel 100x400, 1 disk D=20", params, [50.0], [300.0], [10.0], [0.0])
 
 
-def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision: str = "fp32", hold: int = 1) -> Case:
+def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision: str = "fp32", hold: int = 1,
+                                    diameter: float = 20.0) -> Case:
     """Sedimentation of a disk held at T_c = 0 in a long channel (the paper's
     Sec. 3.3 case, Table 4): D = 20 lu, width 4D, the disk starting D/2
     left of the centreline (x = 1.5 D), rho_r = 1.00232, Re = 40.5, Pr = 0.7,
@@ -124,7 +125,7 @@ def fixed_temperature_sedimentation(gr: float, length_d: float = 80.0, precision
     reading R11b of how the particle is held); fluid and walls at
     T_h = 1 (T_ref = T_h).  The channel length is not given (length_d
     diameters; the disk starts 10 D below the top)."""
-    D = 20.0
+    D = float(diameter)  # 20 cells in the paper (dx = D/20); other values for resolution checks
     nu = (0.53 - 0.5) / 3.0
     u_ref = 40.5 * nu / D
     g = u_ref ** 2 / ((1.00232 - 1.0) * math.pi * D / 2.0)
