@@ -769,8 +769,8 @@ struct BatchGroup {
 };
 
 // Test hook of the persistent step's bounded waits (vlb_debug_batch_wait).
-long long g_wait_ns = 1000000000ll;  // one second
-int g_stuck_handle = -1;
+std::atomic<long long> g_wait_ns{1000000000ll};  // one second
+std::atomic<int> g_stuck_handle{-1};
 
 size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 
@@ -799,7 +799,7 @@ void fill_persistent(PersistentBatch<C>& A, unsigned char* dev, const BatchGroup
   A.ncases = (int)g.handles.size();
   A.with_particles = with_particles ? 1 : 0;
   A.stuck_case = stuck;
-  A.wait_ns = g_wait_ns;
+  A.wait_ns = g_wait_ns.load();
 }
 
 template <class C>
@@ -1004,7 +1004,7 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
       for (auto& g : groups) {
         int stuck = -1;
         for (size_t c = 0; c < g.handles.size(); ++c)
-          if (g.handles[c] == g_stuck_handle) stuck = (int)c;
+          if (g.handles[c] == g_stuck_handle.load()) stuck = (int)c;
         cudaError_t el;
         if (g.f64) {
           PersistentBatch<double> A{};
