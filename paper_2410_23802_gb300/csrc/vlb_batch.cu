@@ -4,6 +4,8 @@
 // that takes the tiles and then the next level's particle steps from a
 // device counter, each particle step after a bounded wait for its case's
 // tiles (form 1).
+#include <atomic>
+
 #include "vlb_lattice_body.cuh"
 #include "vlb_particle_body.cuh"
 
@@ -278,16 +280,19 @@ lattice_persistent_kernel(const __grid_constant__ PersistentBatch<C> A) {
 
 template <class S, class C, bool HOLD>
 static int resident_ctas(int device) {
-  static int cached[64] = {0};
+  // per device, filled by the first call (calls from several host threads
+  // may race to fill it; they store the same value)
+  static std::atomic<int> cached[64];
   if (device < 0 || device >= 64) return 0;
-  if (cached[device] > 0) return cached[device];
+  const int known = cached[device].load(std::memory_order_relaxed);
+  if (known > 0) return known;
   int nb = 0, nsm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lattice_persistent_kernel<S, C, HOLD>, TILE_X * TILE_Y, 0) !=
           cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     return 0;
-  cached[device] = nb * nsm;
-  return cached[device];
+  cached[device].store(nb * nsm, std::memory_order_relaxed);
+  return nb * nsm;
 }
 
 int persistent_grid(int device, bool f64, int storage, bool held) {
