@@ -1037,7 +1037,9 @@ static vlb_status step_batch_impl(vlb_handle* const* hs, int32_t n, int32_t nste
     if (captured) {
       // the executable graph of the last call is kept (per host thread) and
       // updated with this call's launches when they have the same shape, which
-      // costs far less than instantiating one per call
+      // costs far less than instantiating one per call; it lives as long as
+      // the thread (one per thread that ever ran this form: destroying it at
+      // thread exit could run after the CUDA runtime has been unloaded)
       thread_local cudaGraphExec_t cached = nullptr;
       cudaGraph_t graph = nullptr;
       cudaError_t eb = cudaSuccess;
